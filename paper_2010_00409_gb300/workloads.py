@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs and workload parameters.
+
+This module holds no step of the method: only sizes, physical parameters and
+seeded random input fields.  Both the CUDA path and the CPU oracle receive
+their inputs from here (the oracle is never imported by this module).
+
+Units are CGS (Sec. 2.1 of the paper): lengths in cm, times in s,
+c = 2.99792458e10 cm/s.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+C_CGS = 2.99792458e10          # cm/s
+LAMBDA0 = 800e-7               # 800 nm in cm
+
+FLAT_TOP = 0
+GAUSSIAN = 1
+
+
+@dataclass
+class GridSpec:
+    Nx: int
+    Ny: int
+    Nz: int
+    dx: float
+    dy: float
+    dz: float
+    x_min: float = 0.0
+    y_min: float = 0.0
+    z_min: float = 0.0
+    c: float = C_CGS
+
+    @property
+    def D(self) -> float:
+        return self.Nx * self.dx
+
+    @property
+    def cells(self) -> int:
+        return self.Nx * self.Ny * self.Nz
+
+    def courant_dt(self) -> float:
+        """Yee 3D Courant value, used only as a reference step size."""
+        return 1.0 / (self.c * math.sqrt(1 / self.dx ** 2 + 1 / self.dy ** 2 + 1 / self.dz ** 2))
+
+
+@dataclass
+class MappingSpec:
+    R0: float
+    L: float
+
+
+@dataclass
+class PulseSpec:
+    kind: int = FLAT_TOP
+    lam: float = LAMBDA0
+    theta: float = 1.0
+    eps: float = 0.1
+    P0: float = 1e7            # 1 W in erg/s
+    n_cycles: float = 2.0
+    cep: float = 0.0
+    ellipticity: float = 0.0
+    pol_angle: float = 0.0
+    div_project: int = 0
+
+
+# --------------------------------------------------------------------------
+# Plain-method workload: 64^3 periodic box, dx = lambda/16
+# --------------------------------------------------------------------------
+def plain_grid(N: int = 64, lam: float = LAMBDA0, ppw: int = 16) -> GridSpec:
+    d = lam / ppw
+    return GridSpec(N, N, N, d, d, d, 0.0, 0.0, 0.0, C_CGS)
+
+
+def plane_wave_mode(g: GridSpec, periods: int = 4, amplitude: float = 1.0) -> np.ndarray:
+    """x-polarised complex plane wave along +z: E = x^ a e^{i k0 z}, B = y^ a e^{i k0 z},
+    k0 = 2 pi * periods / (Nz dz).  Returns complex128 [6, Nz, Ny, Nx]."""
+    z = g.dz * np.arange(g.Nz)
+    k0 = 2 * np.pi * periods / (g.Nz * g.dz)
+    ph = amplitude * np.exp(1j * k0 * z)[:, None, None] * np.ones((1, g.Ny, g.Nx))
+    f = np.zeros((6, g.Nz, g.Ny, g.Nx), dtype=np.complex128)
+    f[0] = ph
+    f[4] = ph
+    return f
+
+
+def random_divfree_field(g: GridSpec, seed: int, k0: float | None = None,
+                         rms: float = 1e-3) -> np.ndarray:
+    """Seeded random divergence-free E and B (real-valued, complex dtype).
+
+    Each of E and B is the curl of an independent random vector potential with a
+    Gaussian spectrum exp(-|k|^2 / (2 k0^2)); the curl makes it solenoidal by
+    construction.  Each is scaled to the given RMS per component.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if k0 is None:
+        k0 = 2 * np.pi / (16 * g.dx)
+    kx = 2 * np.pi * np.fft.fftfreq(g.Nx, g.dx)[None, None, :]
+    ky = 2 * np.pi * np.fft.fftfreq(g.Ny, g.dy)[None, :, None]
+    kz = 2 * np.pi * np.fft.fftfreq(g.Nz, g.dz)[:, None, None]
+    k2 = kx * kx + ky * ky + kz * kz
+    env = np.exp(-k2 / (2 * k0 * k0))
+    out = np.zeros((6, g.Nz, g.Ny, g.Nx), dtype=np.complex128)
+    for base in (0, 3):
+        a = rng.standard_normal((3, g.Nz, g.Ny, g.Nx))
+        A = np.fft.fftn(a, axes=(-3, -2, -1)) * env
+        cx = 1j * (ky * A[2] - kz * A[1])
+        cy = 1j * (kz * A[0] - kx * A[2])
+        cz = 1j * (kx * A[1] - ky * A[0])
+        v = np.real(np.fft.ifftn(np.stack([cx, cy, cz]), axes=(-3, -2, -1)))
+        s = math.sqrt(float(np.mean(v * v)))
+        out[base:base + 3] = v * (rms / s if s > 0 else 0.0)
+    return out
+
+
+def random_complex_field(shape, seed: int) -> np.ndarray:
+    """Unstructured complex normal field (for FFT / linear-map parity checks)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# --------------------------------------------------------------------------
+# Tight-focus workload: f = 1, 2-cycle Gaussian pulse at 800 nm, R0 = 20 lambda
+# on a 256^3 mapped grid (dx = lambda/16 over D = 16 lambda, y,z in [-18, 18) lambda)
+# --------------------------------------------------------------------------
+def tight_focus_workload(N: int = 256, lam: float = LAMBDA0):
+    """Returns (grid, mapping, pulse, n_steps, plane) for the f = 1 Gaussian focus.
+
+    Geometry: R0 = 20 lam, L = 4.5 * n * lam = 9 lam, D = 16 lam (D_min = 12.6 lam
+    for the pulse's angular support 2*theta0 + 0.1).  x_min = -(R0 - L/2) - D.
+    Time: dt = (R0/c) / n_steps with n_steps = 378 (the Courant value of the
+    256^3 grid), so the last step lands on the focus t = R0/c.
+    Scaled sizes keep the physical box and change the resolution.
+    """
+    R0 = 20 * lam
+    ncyc = 2.0
+    L = 4.5 * ncyc * lam
+    D = 16 * lam
+    W = 36 * lam
+    dx = D / N
+    dyz = W / N
+    R_min = R0 - L / 2
+    g = GridSpec(N, N, N, dx, dyz, dyz, -R_min - D, -W / 2, -W / 2, C_CGS)
+    m = MappingSpec(R0, L)
+    theta0 = math.atan(1.0 / (2.0 * 1.0))
+    p = PulseSpec(kind=GAUSSIAN, lam=lam, theta=theta0, eps=0.2, P0=1e7,
+                  n_cycles=ncyc, cep=0.0, ellipticity=0.0, pol_angle=0.0, div_project=1)
+    n_steps = max(1, int(round(378 * N / 256)))
+    plane = dict(x_p=0.0, ny=128, nz=128, y0=-1.5 * lam, y1=1.5 * lam,
+                 z0=-1.5 * lam, z1=1.5 * lam)
+    return g, m, p, n_steps, plane
+
+
+def flat_top_workload(N: int = 64, lam: float = 1e-4):
+    """The Sec. 3.1 flat-top case (f = 0.3, R0 = 16 lam, L = 2 lam, eps = 0.1,
+    P0 = 1 W) on a small mapped grid with D = 3.5 L (Sec. 3.1)."""
+    R0 = 16 * lam
+    L = 2 * lam
+    D = 3.5 * L
+    W = 40 * lam
+    theta = math.atan(1.0 / (2.0 * 0.3))
+    g = GridSpec(N, N, N, D / N, W / N, W / N, -(R0 - L / 2) - D, -W / 2, -W / 2, C_CGS)
+    m = MappingSpec(R0, L)
+    p = PulseSpec(kind=FLAT_TOP, lam=lam, theta=theta, eps=0.1, P0=1e7, div_project=0)
+    return g, m, p
+
+
+def plane_points(plane: dict):
+    """Sample coordinates of a focal-plane lattice: half-open [y0, y1), [z0, z1)."""
+    ys = plane["y0"] + (plane["y1"] - plane["y0"]) * np.arange(plane["ny"]) / plane["ny"]
+    zs = plane["z0"] + (plane["z1"] - plane["z0"]) * np.arange(plane["nz"]) / plane["nz"]
+    return ys, zs
