@@ -1,0 +1,352 @@
+"""Benchmark of the PSATD tight-focusing path on GB300.
+
+One bench step is one full focal-field job of the f = 1 tight-focus workload on
+the 256^3 mapped grid: pulse initialisation on the periodic layer, 378 PSATD
+steps to the focus t = R0/c, the 128 x 128 focal-plane sample, and the energy /
+divergence diagnostics.  The metric is PSATD cell-steps/s (cells x PSATD steps
+per second) and the fraction of the HBM roofline reached by the dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (the path does not shard); the
+value is the total work of all ranks over the slowest rank's time.
+--impl reference times the float64 CPU oracle on a bounded sample of the same
+workload (one PSATD step on a 256 x 256 x 64 slab of the grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2010_00409_gb300 import workloads as W  # noqa: E402
+
+METRIC = "PSATD cell-steps/s"
+UNIT = "cell-steps/s"
+STEP_KERNELS = ("fft_x", "fft_y", "fft_z", "kspace_z", "plane_xy")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle arm
+def oracle_sample_rate(size: int, reps: int = 1):
+    """One float64 oracle PSATD step on a size x size x size/4 slab of the workload grid."""
+    from oracle import psatd_oracle as O
+    g, m, p, n_steps, plane = W.tight_focus_workload(N=size)
+    nz = max(1, size // 4)
+    og = O.Grid(g.Nx, g.Ny, nz, g.dx, g.dy, g.dz, g.x_min, g.y_min, g.z_min, g.c)
+    rng = np.random.Generator(np.random.PCG64(0))
+    f = rng.standard_normal((6, nz, g.Ny, g.Nx)) + 0j
+    dt = (m.R0 / g.c) / n_steps
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        f = O.psatd_step(f, og, dt)
+        times.append(time.perf_counter() - t0)
+    cells = g.Nx * g.Ny * nz
+    return cells, times, "one float64 oracle PSATD step (numpy pocketfft, 1 thread) on a %dx%dx%d slab of the %d^3 grid" % (
+        g.Nx, g.Ny, nz, size)
+
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    if a.warmup > 0:
+        oracle_sample_rate(a.size, reps=a.warmup)
+    cells, times, sample = oracle_sample_rate(a.size, reps=a.steps)
+    t = sum(times)
+    value = cells * a.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(a.size),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(size):
+    g, m, p, n_steps, plane = W.tight_focus_workload(N=size)
+    return {"workload": "tight focus f=1, 2-cycle Gaussian at 800 nm, R0=20 lambda, %d^3 mapped grid, "
+                        "%d PSATD steps to focus + 128x128 focal plane + diagnostics" % (size, n_steps),
+            "grid": [g.Nx, g.Ny, g.Nz], "psatd_steps_per_job": n_steps, "precision": "fp32 storage/arithmetic, "
+            "fp64 tables/coordinates/reductions", "layout": "SoA [6][Nz][Ny][Nx] complex64",
+            "l2": "inputs larger than L2 (field %.0f MB > 129 MB L2)" % (6 * g.cells * 8 / 1e6),
+            "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    from paper_2010_00409_gb300 import psatd
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    g, m, p, n_steps, plane = W.tight_focus_workload(N=a.size)
+    dt = (m.R0 / g.c) / n_steps
+    stream = torch.cuda.Stream(dev)
+    ctx = psatd.Context(g, m, dt, 32, stream=stream)
+    out_dev = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
+
+    def job(c, out):
+        c.init_pulse(p)
+        c.advance(n_steps)
+        c.sample_focal_plane(plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"],
+                             plane["z0"], plane["z1"], comps=(0, 1, 2), out=out)
+        return c.diagnostics()
+
+    for _ in range(a.warmup):
+        job(ctx, out_dev)
+    ctx.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ctx.profile_enable(True)
+    n0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        diag = job(ctx, out_dev)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = ctx.launch_count - n0
+    t_ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    t_max = t_ms
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    cell_steps = g.cells * n_steps * a.steps * world
+    value = cell_steps / (t_max / 1e3)
+
+    # roofline of the dominant per-step kernel: algorithmic bytes = one read and one
+    # write of the six complex64 components (96 B per cell) per launch
+    peak, peak_src = measured_peaks()
+    step_k = {k: v for k, v in prof.items() if k in STEP_KERNELS}
+    dom = max(step_k, key=lambda k: step_k[k][0])
+    dom_ms, dom_n = step_k[dom]
+    bytes_per_launch = 96 * g.cells
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    step_total = sum(v[0] for v in step_k.values())
+    all_total = sum(v[0] for v in prof.values())
+    # whole-step HBM figure: 3 sweeps of 96 B per cell-step is the design floor
+    sweep_bytes = sum(96 * g.cells * v[1] for k, v in step_k.items())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(a.size),
+        "focal_fields_per_s": world * a.steps / (t_max / 1e3),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": None, "bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": dom_ms / dom_n, "launches": dom_n},
+        "kernel_share": {k: round(v[0] / all_total, 4) for k, v in sorted(prof.items())},
+        "step_hbm": {"algorithmic_bytes_per_cell_step": sweep_bytes / (g.cells * n_steps * a.steps),
+                     "achieved_GBps": sweep_bytes / (step_total / 1e3) / 1e9,
+                     "frac_of_288B_design": (288 * g.cells * n_steps * a.steps) / (step_total / 1e3) / 1e9 / peak,
+                     "frac_of_96B_floor": (96 * g.cells * n_steps * a.steps) / (step_total / 1e3) / 1e9 / peak},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "diag_last": {"energy": diag["energy"], "max_div_E_rel": diag["max_div_E"] / max(diag["max_E_hat"], 1e-300)},
+    }
+
+    if not a.no_e2e:
+        line["e2e"] = e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world)
+    if not a.no_fp64:
+        line["fp64"] = fp64_measure(g, m, p, n_steps, dt, dev, stream)
+    ctx.close()
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cells, times, sample = oracle_sample_rate(a.size, reps=1)
+        line["cpu_baseline"] = {"value": cells / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world):
+    """The same job through the public API with host buffers: the initial six
+    components come from pinned host memory (set_field), the focal plane and the
+    diagnostics go back to the host, every step."""
+    import torch
+    ctx.init_pulse(p)
+    host_in = torch.empty((6, g.Nz, g.Ny, g.Nx), dtype=torch.complex64, pin_memory=True)
+    host_in.copy_(ctx.fields.cpu())
+    host_out = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, pin_memory=True)
+    import ctypes as C
+    from paper_2010_00409_gb300 import psatd
+    L = psatd.lib()
+
+    def step():
+        psatd._check(L.psatd_set_field(ctx._ptr, -1, C.c_void_p(host_in.data_ptr()), 0), ctx._ptr)
+        ctx.set_time(0.0)
+        ctx.advance(n_steps)
+        psatd._check(L.psatd_sample_focal_plane(
+            ctx._ptr, plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"],
+            plane["z1"], 7, C.c_void_p(host_out.data_ptr()), 0), ctx._ptr)
+        return ctx.diagnostics()
+
+    step()
+    ctx.synchronize()
+    k = max(1, min(a.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    ctx.synchronize()
+    t = time.perf_counter() - t0
+    return {"value": world * g.cells * n_steps * k / t, "unit": UNIT,
+            "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+            "d2h_bytes_per_step": host_out.numel() * host_out.element_size() + 7 * 8,
+            "steps": k, "ms_per_step": 1e3 * t / k}
+
+
+def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
+    """The plain float64 GPU solver on the same grid: n PSATD steps."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    with psatd.Context(g, m, dt, 64, stream=stream) as c:
+        c.init_pulse(p)
+        c.advance(2)
+        c.synchronize()
+        c.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.advance(n)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        prof = c.profile_read()
+    return {"value": g.cells * n / (ms / 1e3), "unit": UNIT, "psatd_steps": n, "ms_per_psatd_step": ms / n,
+            "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()}}
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * psatd.h -- C ABI of the GB300 PSATD tight-focusing library.
+ *
+ * The library advances an electromagnetic pulse in vacuum with the analytic-in-
+ * time spectral (PSATD) Maxwell solver of arXiv:2010.00409, Sec. 2.1 (Eq. 3-4),
+ * on the periodic layer produced by the mapping of Sec. 2.3 (Eq. 13), and maps
+ * the result back to physical space with the cut-out of Eq. 14-16.
+ *
+ * Conventions shared by every entry point:
+ *  - Units are those of the caller; the paper uses CGS (Sec. 2.1).  c is passed.
+ *  - Field storage is six complex components in the order Ex, Ey, Ez, Bx, By, Bz,
+ *    component-major, each [Nz][Ny][Nx] with x fastest ("SoA").  Precision 32
+ *    stores float2 (8 B per value, 48 B per cell); precision 64 stores double2
+ *    (16 B per value, 96 B per cell).  Node (i, j, l) sits at
+ *    (x_min + i*dx, y_min + j*dy, z_min + l*dz).
+ *  - The forward DFT is unnormalised with kernel exp(-i k.x); wave numbers are
+ *    k_m = 2*pi*m/(N*d), m in {-floor(N/2), ..., ceil(N/2)-1} (numpy order), so the
+ *    Nyquist index of even N is -N/2.  At k = 0 the unit vector k^ is 0.
+ *  - Every call returns a psatd_status; nothing throws or aborts across the ABI.
+ *    On error the context keeps its previous state and psatd_last_error() holds
+ *    a one-line message.
+ *  - Work is enqueued on the CUDA stream given to psatd_init_grid and is
+ *    asynchronous, except where a call says it synchronises.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Host pointers are plain pageable or pinned memory owned by the caller;
+ *    device pointers are owned by the caller unless stated otherwise.
+ *  - Sizes: every N must be 1..2048 and factor into 2, 3 and 5 (else
+ *    PSATD_ERR_SIZE).
+ */
+#ifndef PSATD_H
+#define PSATD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psatd_ctx psatd_ctx;
+
+typedef enum psatd_status {
+    PSATD_OK = 0,
+    PSATD_ERR_ARG = -1,      /* NULL pointer, bad enum, non-finite or inconsistent value */
+    PSATD_ERR_SIZE = -2,     /* N outside 1..2048 or with a prime factor other than 2, 3, 5 */
+    PSATD_ERR_OOM = -3,      /* a device allocation failed */
+    PSATD_ERR_CUDA = -4,     /* a CUDA runtime call or kernel launch failed */
+    PSATD_ERR_TIMEOUT = -5,  /* a bounded device wait expired */
+    PSATD_ERR_STATE = -6     /* call not valid in the current state (e.g. no fields) */
+} psatd_status;
+
+enum { PSATD_PULSE_FLAT_TOP = 0, PSATD_PULSE_GAUSSIAN = 1 };
+enum { PSATD_FORWARD = -1, PSATD_INVERSE = +1 };
+enum { PSATD_FLAG_NO_FIELD_ALLOC = 1 };   /* init_grid: caller binds field storage */
+
+/* The periodic box (Sec. 2.3): D = Nx*dx is the period of the mapped layer. */
+typedef struct psatd_grid {
+    int Nx, Ny, Nz;
+    double dx, dy, dz;
+    double x_min, y_min, z_min;   /* node (0,0,0); Eq. 13 layer uses x_min = -R_min - D */
+    double c;                     /* speed of light (CGS: 2.99792458e10 cm/s) */
+} psatd_grid;
+
+/* Geometry of the initial spherical shell R0 - L/2 <= R <= R0 + L/2 (Sec. 2.2);
+ * used by the pulse models and by the cut-out I_S of Eq. 15-16. */
+typedef struct psatd_mapping {
+    double R0;
+    double L;
+} psatd_mapping;
+
+/* Pulse models.  FLAT_TOP is Eq. 5-11 (u = A/R u_l(R-R0) u_ts(alpha), A of Eq. 9,
+ * E = u s0, B = u s1).  GAUSSIAN is Sec. 3.2.1: u = E0 R0 sin(k(R-R0)+phi) u_l u_ts / R
+ * with u_l = exp(-zeta^2 ln4/(n lambda)^2) on |zeta| <= L/2 and
+ * u_ts = exp(-alpha^2/theta0^2) times the Eq. 5 edge at 2*theta0 with width eps;
+ * E0 = sqrt(4 P0 / (c R0^2 F(theta0))) with the series F of Sec. 3.2.1 (CGS form).
+ * alpha is the angle from the -x axis; s0 = |R x (d x R)|^-1 R x (d x R) and
+ * s1 = |d x R|^-1 d x R; d1 = (0, cos psi, sin psi), d2 = (0, -sin psi, cos psi);
+ * E = u_phi s0(d1) + e u_{phi+pi/2} s0(d2) and likewise B with s1.  Replicas of the
+ * pulse spaced D along x are summed at every node (Sec. 2.3). */
+typedef struct psatd_pulse {
+    int kind;            /* PSATD_PULSE_FLAT_TOP or PSATD_PULSE_GAUSSIAN */
+    int div_project;     /* nonzero: remove k^(k^.E) and k^(k^.B) once after init (Sec. 2.1) */
+    double lambda;       /* carrier wavelength */
+    double theta;        /* flat-top half angle theta; Gaussian theta0 */
+    double eps;          /* edge smoothing angle of Eq. 5 */
+    double P0;           /* power (cycle-averaged, as Eq. 9 and Sec. 3.2.1) */
+    double n_cycles;     /* Gaussian FWHM duration in wavelengths (n of Sec. 3.2.1) */
+    double cep;          /* carrier phase phi */
+    double ellipticity;  /* e in [0, 1] */
+    double pol_angle;    /* psi */
+} psatd_pulse;
+
+/* Energy and spectral divergence of the current fields. */
+typedef struct psatd_diag {
+    double energy;       /* sum over cells of |E|^2 + |B|^2 */
+    double energy_E;
+    double energy_B;
+    double max_div_E;    /* max over k of |k^ . FFT(E)(k)| (unnormalised DFT) */
+    double max_div_B;
+    double max_E_hat;    /* max over k of |FFT(E)(k)| (vector norm) */
+    double max_B_hat;
+} psatd_diag;
+
+/* Create a context for one periodic box and allocate its tables (and, unless
+ * flags has PSATD_FLAG_NO_FIELD_ALLOC, the six-component field storage, zeroed).
+ * dt is the step of psatd_advance; precision is 32 or 64; cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The mapping geometry is only
+ * needed by psatd_init_pulse and psatd_sample_focal_plane.
+ * Cites: Sec. 2.1 (solver), Sec. 2.3 (periodic layer). */
+psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mapping,
+                             double dt, int precision, void* cuda_stream, int flags,
+                             psatd_ctx** out);
+
+/* Release everything the context owns (not caller-bound field storage). */
+void psatd_destroy(psatd_ctx* ctx);
+
+/* Change the step; rebuilds the cos/sin table on the host in float64.  Any finite
+ * dt is valid, including negative (time reversal) and large (Sec. 2.1: the
+ * vacuum solver is exact in time for any step). */
+psatd_status psatd_set_dt(psatd_ctx* ctx, double dt);
+
+/* Use caller-owned device memory (e.g. a torch tensor) as the field storage.
+ * bytes must be at least 6*Nx*Ny*Nz*(8 or 16) and dev_ptr 256-byte aligned.
+ * Library-owned storage, if any, is freed.  The memory must outlive the context
+ * or the next bind. */
+psatd_status psatd_bind_fields(psatd_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Device pointer and size of the current field storage. */
+psatd_status psatd_fields(psatd_ctx* ctx, void** dev_ptr, size_t* bytes);
+
+/* Copy component comp (0..5, or -1 for all six) from src, laid out as the field
+ * storage of that component(s).  src_on_device selects device or host memory.
+ * Host copies synchronise the stream. */
+psatd_status psatd_set_field(psatd_ctx* ctx, int comp, const void* src, int src_on_device);
+psatd_status psatd_get_field(psatd_ctx* ctx, int comp, void* dst, int dst_on_device);
+
+/* Initialise all six components from a pulse model on the mapped grid (Eq. 5-13,
+ * Sec. 3.2.1).  Coordinates and the pulse are evaluated in float64 and rounded
+ * once.  Resets the time to 0. */
+psatd_status psatd_init_pulse(psatd_ctx* ctx, const psatd_pulse* pulse);
+
+/* Advance n_steps >= 0 PSATD steps of size dt (Eq. 3-4): per step a forward 3D
+ * FFT of the six components, the per-mode update, and an inverse 3D FFT; the
+ * physical field is in storage after every step.  Asynchronous. */
+psatd_status psatd_advance(psatd_ctx* ctx, int n_steps);
+
+/* In-place 3D DFT of all six components with the library's FFT kernels:
+ * direction PSATD_FORWARD (exp(-ikx)) or PSATD_INVERSE (exp(+ikx)); both
+ * unnormalised.  Asynchronous. */
+psatd_status psatd_fft(psatd_ctx* ctx, int direction);
+
+/* Sample the physical field on the plane x = x_phys at y_p = y0 + p (y1-y0)/ny,
+ * z_q = z0 + q (z1-z0)/nz (p < ny, q < nz) at the current time t, as
+ * u(R, t) = u~(T(R)) I_S(t)(R) (Eq. 13-16) with u~ the exact trigonometric
+ * interpolant of the grid field.  comp_mask selects components (bit c = component
+ * c); dst receives popcount(comp_mask) planes [nz][ny] of complex values in the
+ * context precision, in increasing component order.  Synchronises when dst is
+ * on the host.  ny, nz in 1..4096. */
+psatd_status psatd_sample_focal_plane(psatd_ctx* ctx, double x_phys, int ny, int nz,
+                                      double y0, double y1, double z0, double z1,
+                                      int comp_mask, void* dst, int dst_on_device);
+
+/* Energy and spectral divergence of the current fields (float64 accumulation).
+ * Synchronises. */
+psatd_status psatd_diagnostics(psatd_ctx* ctx, psatd_diag* out);
+
+/* Current time t = (steps taken since init_pulse or set_time) * dt, summed. */
+double psatd_time(const psatd_ctx* ctx);
+psatd_status psatd_set_time(psatd_ctx* ctx, double t);
+
+/* Wait for all work of the context's stream. */
+psatd_status psatd_synchronize(psatd_ctx* ctx);
+
+/* Eq. 12: D_min = -R_min cos(theta) + sqrt(R_max^2 - R_min^2 sin^2(theta)). */
+double psatd_d_min(double R0, double L, double theta);
+
+/* Message of the last failed call on ctx (or of the last failed psatd_init_grid
+ * when ctx is NULL).  Never NULL. */
+const char* psatd_last_error(const psatd_ctx* ctx);
+
+/* Static name of a status code. */
+const char* psatd_status_string(psatd_status s);
+
+/* Number of kernel launches the context has issued since creation. */
+long long psatd_launch_count(const psatd_ctx* ctx);
+
+/* Kernel kinds for per-kernel timing. */
+enum {
+    PSATD_KERNEL_FFT_X = 0,      /* generic FFT along x */
+    PSATD_KERNEL_FFT_Y = 1,      /* generic FFT along y */
+    PSATD_KERNEL_FFT_Z = 2,      /* generic FFT along z */
+    PSATD_KERNEL_KSPACE = 3,     /* fused z-FFT / per-mode update / inverse z-FFT */
+    PSATD_KERNEL_INIT = 4,       /* pulse initialisation */
+    PSATD_KERNEL_SAMPLE = 5,     /* focal-plane sampling (all of its launches) */
+    PSATD_KERNEL_DIAG = 6,       /* energy / divergence reductions */
+    PSATD_KERNEL_PLANE_XY = 7,   /* fused x+y plane FFT */
+    PSATD_KERNEL_KINDS = 8
+};
+
+/* Start (enable != 0) or stop per-kernel timing: while enabled every launch of
+ * the context is bracketed by a pair of CUDA events on its stream.  Enabling
+ * clears the accumulated totals. */
+psatd_status psatd_profile_enable(psatd_ctx* ctx, int enable);
+
+/* Accumulated device time (ms) and number of timed launches of one kernel kind
+ * since profiling was enabled.  Synchronises the stream. */
+psatd_status psatd_profile_read(psatd_ctx* ctx, int kind, double* total_ms, long long* launches);
+
+/* Static name of a kernel kind ("fft_x", ...). */
+const char* psatd_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSATD_H */

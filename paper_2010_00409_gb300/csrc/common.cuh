@@ -1,0 +1,130 @@
+// Shared device/host helpers of the PSATD library: complex arithmetic, the
+// per-axis FFT plan, and the launch interfaces of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psatd {
+
+// ---------------------------------------------------------------------------
+// complex helpers over float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct vec2;
+template <> struct vec2<float>  { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using cplx = typename vec2<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T re, T im) {
+    cplx<T> r; r.x = re; r.y = im; return r;
+}
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+    V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename V> __host__ __device__ __forceinline__ V cmulc(V a, V b) {
+    V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+// multiply by s*i, s = +-1
+template <typename V> __host__ __device__ __forceinline__ V cmul_si(V a, int s) {
+    V r; if (s > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r;
+}
+
+// ---------------------------------------------------------------------------
+// 1D plan of one axis: N = prod(radix[0..npass)), radices in {2,3,4,5,8}
+// ---------------------------------------------------------------------------
+constexpr int kMaxPass = 16;
+struct AxisPlan {
+    int N;
+    int npass;
+    int radix[kMaxPass];
+};
+
+// Host: factor N into 8, 4, 5, 3, 2 (largest radices first).  Returns false if
+// N has another prime factor.
+bool make_plan(int N, AxisPlan* p);
+
+// ---------------------------------------------------------------------------
+// Per-mode table entry: C/Ntot, S/Ntot, 1/|k| (0 at k = 0).
+// Indexed by (|m_z|, |m_y|, |m_x|), each 0..N/2.
+// ---------------------------------------------------------------------------
+template <typename T> struct alignas(4 * sizeof(T)) ModeCoef { T C, S, kinv, pad; };
+
+// Geometry handed to the kernels (all float64).
+struct GridGeom {
+    int Nx, Ny, Nz;
+    double dx, dy, dz;
+    double x_min, y_min, z_min;
+    double c;
+};
+
+struct ShellGeom { double R0, L; };
+
+struct PulseParams {
+    int kind, div_project;
+    double lambda, theta, eps, P0, n_cycles, cep, ellipticity, pol_angle;
+    double amp;          // A (flat-top) or E0 (Gaussian), computed on the host
+};
+
+// Device tables of one context.
+template <typename T> struct Tables {
+    const cplx<T>* tw[3];       // tw[a][t] = exp(-2 pi i t / N_a), t < N_a
+    const T* k[3];              // k_a[i] = 2 pi m(i) / (N_a d_a)
+    const ModeCoef<T>* coef;    // (Nz/2+1) x (Ny/2+1) x (Nx/2+1)
+    AxisPlan plan[3];
+};
+
+// K2 modes
+enum KspaceMode { KS_ROTATE = 0, KS_PROJECT = 1 };
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (one translation unit each); all return cudaGetLastError().
+// ---------------------------------------------------------------------------
+// In-place FFT along one axis (0 = x, 1 = y, 2 = z) of ncomp consecutive
+// components of an [ncomp][Nz][Ny][Nx] array.  dir = -1 forward, +1 inverse.
+template <typename T>
+cudaError_t launch_fft_axis(cplx<T>* data, int ncomp, const GridGeom& g, const Tables<T>& tb,
+                            int axis, int dir, cudaStream_t s, long long* nlaunch);
+
+// Fused z-forward FFT, per-mode update, z-inverse FFT over all six components.
+template <typename T>
+cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode,
+                            double scale, cudaStream_t s, long long* nlaunch);
+
+// Pulse initialisation on the mapped grid.
+template <typename T>
+cudaError_t launch_init_pulse(cplx<T>* data, const GridGeom& g, const ShellGeom& sh,
+                              const PulseParams& p, int m_lo, int m_hi, cudaStream_t s,
+                              long long* nlaunch);
+
+// Focal-plane sampling scratch and launch.
+struct SampleScratch {
+    double2* wx;     // [Nx]
+    double2* wy;     // [ny][Ny]
+    double2* wz;     // [nz][Nz]
+    double2* g;      // [ncomp][Nz][Ny]
+    double2* h;      // [ncomp][Nz][ny]
+};
+template <typename T>
+cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const ShellGeom& sh,
+                                double x_phys, int ny, int nz, double y0, double y1, double z0,
+                                double z1, double t, const int* comps, int ncomp,
+                                const SampleScratch& sc, cplx<T>* out, cudaStream_t s,
+                                long long* nlaunch);
+
+// Diagnostics: energy partials and spectral divergence partials.
+template <typename T>
+cudaError_t launch_energy(const cplx<T>* data, size_t n_per_comp, double* partial, int nblocks,
+                          cudaStream_t s, long long* nlaunch);
+template <typename T>
+cudaError_t launch_divergence(const cplx<T>* spec3, const GridGeom& g, const Tables<T>& tb,
+                              double* partial, int nblocks, cudaStream_t s, long long* nlaunch);
+// Final reduction of `nblocks` rows of `width` doubles: columns [0, nsum) are
+// summed, columns [nsum, width) are max-reduced.  Result in out[width].
+cudaError_t launch_reduce_final(const double* partial, int nblocks, int width, int nsum,
+                                double* out, cudaStream_t s, long long* nlaunch);
+
+}  // namespace psatd

@@ -1,0 +1,156 @@
+// Device FFT building blocks: radix-2/3/4/5/8 butterflies and a Stockham
+// (self-sorting) pass over a tile of pencils held in shared memory.
+//
+// Sign convention: S = -1 is the forward transform (kernel exp(-2 pi i nk/N)),
+// S = +1 the inverse; neither is normalised.
+//
+// Stockham decimation-in-time, mixed radix: after the passes with radices
+// R_1..R_{p-1} (product Ns), pass p with radix R reads element j + r*N/R of the
+// input (r < R, j < N/R), multiplies it by exp(S 2 pi i r (j mod Ns)/(Ns R)),
+// applies the R-point DFT and writes the outputs to
+// (j div Ns)*Ns*R + (j mod Ns) + r*Ns.  After the last pass the data are in
+// natural order.
+#pragma once
+
+#include "common.cuh"
+
+namespace psatd {
+
+template <typename V, int S>
+__host__ __device__ __forceinline__ void bfly2(V& a0, V& a1) {
+    V t = a0; a0 = cadd(t, a1); a1 = csub(t, a1);
+}
+
+template <typename V, int S>
+__host__ __device__ __forceinline__ void bfly4(V& a0, V& a1, V& a2, V& a3) {
+    V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+    V t3 = cmul_si(csub(a1, a3), S);
+    a0 = cadd(t0, t2); a2 = csub(t0, t2);
+    a1 = cadd(t1, t3); a3 = csub(t1, t3);
+}
+
+template <typename T, int S>
+__host__ __device__ __forceinline__ void bfly8(cplx<T>* v) {
+    // even / odd 4-point DFTs, then combine with exp(S 2 pi i k / 8)
+    bfly4<cplx<T>, S>(v[0], v[2], v[4], v[6]);
+    bfly4<cplx<T>, S>(v[1], v[3], v[5], v[7]);
+    const T r = (T)0.70710678118654752440;
+    cplx<T> o1 = v[3], o2 = v[5], o3 = v[7];
+    // W^1 = (1 + S i)/sqrt2
+    cplx<T> w1 = mk<T>(r * (o1.x - S * o1.y), r * (o1.y + S * o1.x));
+    // W^2 = S i
+    cplx<T> w2 = cmul_si(o2, S);
+    // W^3 = (-1 + S i)/sqrt2
+    cplx<T> w3 = mk<T>(-r * (o3.x + S * o3.y), r * (S * o3.x - o3.y));
+    cplx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, w1); v[5] = csub(e1, w1);
+    v[2] = cadd(e2, w2); v[6] = csub(e2, w2);
+    v[3] = cadd(e3, w3); v[7] = csub(e3, w3);
+}
+
+template <typename T, int S>
+__host__ __device__ __forceinline__ void bfly3(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2) {
+    const T h = (T)0.86602540378443864676;   // sin(2 pi / 3)
+    cplx<T> t = cadd(a1, a2), u = csub(a1, a2);
+    cplx<T> m = mk<T>(a0.x - (T)0.5 * t.x, a0.y - (T)0.5 * t.y);
+    cplx<T> v = cmul_si(cscale(u, h), S);
+    a0 = cadd(a0, t);
+    a1 = cadd(m, v);
+    a2 = csub(m, v);
+}
+
+template <typename T, int S>
+__host__ __device__ __forceinline__ void bfly5(cplx<T>* a) {
+    const T c1 = (T)0.30901699437494742410;    // cos(2 pi / 5)
+    const T c2 = (T)-0.80901699437494742410;   // cos(4 pi / 5)
+    const T s1 = (T)0.95105651629515357212;    // sin(2 pi / 5)
+    const T s2 = (T)0.58778525229247312917;    // sin(4 pi / 5)
+    cplx<T> t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+    cplx<T> u1 = csub(a[1], a[4]), u2 = csub(a[2], a[3]);
+    cplx<T> a0 = a[0];
+    cplx<T> p1 = mk<T>(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+    cplx<T> p2 = mk<T>(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+    cplx<T> q1 = cmul_si(mk<T>(s1 * u1.x + s2 * u2.x, s1 * u1.y + s2 * u2.y), S);
+    cplx<T> q2 = cmul_si(mk<T>(s2 * u1.x - s1 * u2.x, s2 * u1.y - s1 * u2.y), S);
+    a[0] = cadd(a0, cadd(t1, t2));
+    a[1] = cadd(p1, q1);
+    a[4] = csub(p1, q1);
+    a[2] = cadd(p2, q2);
+    a[3] = csub(p2, q2);
+}
+
+template <typename T, int R, int S>
+__host__ __device__ __forceinline__ void dft_r(cplx<T>* v) {
+    if constexpr (R == 2) bfly2<cplx<T>, S>(v[0], v[1]);
+    else if constexpr (R == 3) bfly3<T, S>(v[0], v[1], v[2]);
+    else if constexpr (R == 4) bfly4<cplx<T>, S>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 5) bfly5<T, S>(v);
+    else if constexpr (R == 8) bfly8<T, S>(v);
+}
+
+// One Stockham pass over `W` pencils of length N stored with stride P in
+// `in`, written to `out`.  Work items b = tid, tid + nthr, ... < W*N/R.
+// tw[t] = exp(-2 pi i t / N); the inverse uses its conjugate.
+template <typename T, int R, int S>
+__host__ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in,
+                                                       cplx<T>* __restrict__ out, int N, int Ns,
+                                                       int W, int P, const cplx<T>* __restrict__ tw,
+                                                       int tid, int nthr) {
+    const int nb = N / R;
+    const int tstride = N / (Ns * R);
+    for (int b = tid; b < W * nb; b += nthr) {
+        const int w = b / nb;
+        const int j = b - w * nb;
+        const cplx<T>* src = in + (size_t)w * P;
+        cplx<T>* dst = out + (size_t)w * P;
+        cplx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+        const int k = j % Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const cplx<T> wv = tw[(r * k) * tstride];
+                v[r] = (S < 0) ? cmul(v[r], wv) : cmulc(v[r], wv);
+            }
+        }
+        dft_r<T, R, S>(v);
+        const int idx = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[idx + r * Ns] = v[r];
+    }
+}
+
+template <typename T, int S>
+__host__ __device__ __forceinline__ void stockham_dispatch(int R, const cplx<T>* in, cplx<T>* out,
+                                                           int N, int Ns, int W, int P,
+                                                           const cplx<T>* tw, int tid, int nthr) {
+    switch (R) {
+        case 2: stockham_pass<T, 2, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
+        case 3: stockham_pass<T, 3, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
+        case 4: stockham_pass<T, 4, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
+        case 5: stockham_pass<T, 5, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
+        default: stockham_pass<T, 8, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
+    }
+}
+
+#ifdef __CUDACC__
+// Full transform of a shared-memory tile, ping-ponging between a and b.
+// Returns the buffer that holds the result.  Must be called by the whole block.
+template <typename T, int S>
+__device__ __forceinline__ cplx<T>* fft_tile(cplx<T>* a, cplx<T>* b, const AxisPlan& pl, int W,
+                                             int P, const cplx<T>* tw) {
+    int Ns = 1;
+    for (int p = 0; p < pl.npass; ++p) {
+        const int R = pl.radix[p];
+        stockham_dispatch<T, S>(R, a, b, pl.N, Ns, W, P, tw, threadIdx.x, blockDim.x);
+        __syncthreads();
+        cplx<T>* t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+#endif
+
+}  // namespace psatd

@@ -1,0 +1,682 @@
+// C ABI of the PSATD library (declared in include/psatd.h): argument checks,
+// float64 host tables, device memory, and the order of kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/psatd.h"
+#include "common.cuh"
+
+using namespace psatd;
+
+namespace psatd {
+
+bool make_plan(int N, AxisPlan* p) {
+    p->N = N;
+    p->npass = 0;
+    int n = N;
+    const int rs[5] = {8, 4, 5, 3, 2};
+    for (int r : rs) {
+        while (n % r == 0 && p->npass < kMaxPass) {
+            p->radix[p->npass++] = r;
+            n /= r;
+        }
+    }
+    return n == 1;
+}
+
+}  // namespace psatd
+
+namespace {
+
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr int kMaxN = 2048;
+constexpr int kDiagBlocks = 1024;
+
+thread_local std::string g_create_error = "no error";
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct psatd_ctx {
+    psatd_grid grid{};
+    psatd_mapping mapping{};
+    double dt = 0.0;
+    double t = 0.0;
+    int prec = 32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // fields
+    void* fields = nullptr;
+    size_t field_bytes = 0;
+    bool own_fields = false;
+
+    // tables (device)
+    DevBuf tw[3], k[3], coef;
+    AxisPlan plan[3];
+
+    // scratch (device), allocated on first use
+    DevBuf diag_spec, diag_partial, diag_out;
+    DevBuf samp_wx, samp_wy, samp_wz, samp_g, samp_h, samp_out;
+    int samp_ny = 0, samp_nz = 0;
+
+    long long launches = 0;
+    std::string err = "no error";
+
+    // per-kernel event timing (psatd_profile_enable)
+    struct Pending { cudaEvent_t a, b; int kind; };
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Pending> pending;
+    double prof_ms[PSATD_KERNEL_KINDS] = {0};
+    long long prof_n[PSATD_KERNEL_KINDS] = {0};
+};
+
+namespace {
+
+psatd_status fail(psatd_ctx* c, psatd_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+psatd_status cuda_fail(psatd_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? PSATD_ERR_OOM : PSATD_ERR_CUDA, m);
+}
+
+#define CK(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)
+
+size_t cplx_size(int prec) { return prec == 64 ? 16 : 8; }
+size_t n_cells(const psatd_grid& g) { return (size_t)g.Nx * g.Ny * g.Nz; }
+
+void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaError_t ensure_buf(DevBuf& b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return cudaSuccess;
+    free_buf(b);
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.bytes = bytes;
+    else b.p = nullptr;
+    return e;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+GridGeom geom(const psatd_ctx* c) {
+    GridGeom g;
+    g.Nx = c->grid.Nx; g.Ny = c->grid.Ny; g.Nz = c->grid.Nz;
+    g.dx = c->grid.dx; g.dy = c->grid.dy; g.dz = c->grid.dz;
+    g.x_min = c->grid.x_min; g.y_min = c->grid.y_min; g.z_min = c->grid.z_min;
+    g.c = c->grid.c;
+    return g;
+}
+
+template <typename T>
+Tables<T> tables(const psatd_ctx* c) {
+    Tables<T> tb;
+    for (int a = 0; a < 3; ++a) {
+        tb.tw[a] = static_cast<const cplx<T>*>(c->tw[a].p);
+        tb.k[a] = static_cast<const T*>(c->k[a].p);
+        tb.plan[a] = c->plan[a];
+    }
+    tb.coef = static_cast<const ModeCoef<T>*>(c->coef.p);
+    return tb;
+}
+
+int axis_n(const psatd_grid& g, int a) { return a == 0 ? g.Nx : (a == 1 ? g.Ny : g.Nz); }
+double axis_d(const psatd_grid& g, int a) { return a == 0 ? g.dx : (a == 1 ? g.dy : g.dz); }
+
+// signed index m of position i in numpy fftfreq order
+int freq_index(int i, int N) { return i <= (N - 1) / 2 ? i : i - N; }
+
+template <typename T>
+psatd_status upload_axis_tables(psatd_ctx* c) {
+    for (int a = 0; a < 3; ++a) {
+        const int N = axis_n(c->grid, a);
+        const double d = axis_d(c->grid, a);
+        std::vector<cplx<T>> tw(N);
+        std::vector<T> k(N);
+        for (int t = 0; t < N; ++t) {
+            const double ang = kTwoPi * (double)t / (double)N;
+            tw[t] = mk<T>((T)std::cos(ang), (T)(-std::sin(ang)));
+            k[t] = (T)(kTwoPi * (double)freq_index(t, N) / (N * d));
+        }
+        CK(c, ensure_buf(c->tw[a], N * sizeof(cplx<T>)));
+        CK(c, ensure_buf(c->k[a], N * sizeof(T)));
+        CK(c, cudaMemcpy(c->tw[a].p, tw.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+        CK(c, cudaMemcpy(c->k[a].p, k.data(), N * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    return PSATD_OK;
+}
+
+// (C/Ntot, S/Ntot, 1/|k|) per |m| octant, float64 then rounded once.
+template <typename T>
+psatd_status upload_coef(psatd_ctx* c, double dt) {
+    const psatd_grid& g = c->grid;
+    const int hx = g.Nx / 2 + 1, hy = g.Ny / 2 + 1, hz = g.Nz / 2 + 1;
+    const double ntot = (double)n_cells(g);
+    std::vector<ModeCoef<T>> tab((size_t)hx * hy * hz);
+    for (int az = 0; az < hz; ++az) {
+        const double kz = kTwoPi * az / (g.Nz * g.dz);
+        for (int ay = 0; ay < hy; ++ay) {
+            const double ky = kTwoPi * ay / (g.Ny * g.dy);
+            for (int ax = 0; ax < hx; ++ax) {
+                const double kx = kTwoPi * ax / (g.Nx * g.dx);
+                const double km = std::sqrt(kx * kx + ky * ky + kz * kz);
+                ModeCoef<T> m;
+                m.C = (T)(std::cos(g.c * km * dt) / ntot);
+                m.S = (T)(std::sin(g.c * km * dt) / ntot);
+                m.kinv = (T)(km > 0 ? 1.0 / km : 0.0);
+                m.pad = (T)0;
+                tab[((size_t)az * hy + ay) * hx + ax] = m;
+            }
+        }
+    }
+    const size_t bytes = tab.size() * sizeof(ModeCoef<T>);
+    CK(c, ensure_buf(c->coef, bytes));
+    CK(c, cudaMemcpyAsync(c->coef.p, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PSATD_OK;
+}
+
+psatd_status set_coef(psatd_ctx* c, double dt) {
+    return c->prec == 64 ? upload_coef<double>(c, dt) : upload_coef<float>(c, dt);
+}
+
+psatd_status check_ctx(psatd_ctx* c, bool need_fields) {
+    if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
+    if (need_fields && !c->fields) return fail(c, PSATD_ERR_STATE, "no field storage bound");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return PSATD_OK;
+}
+
+cudaEvent_t take_event(psatd_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Move finished (or, with wait, the oldest `upto`) event pairs into the totals.
+cudaError_t harvest(psatd_ctx* c, size_t upto) {
+    size_t i = 0;
+    for (; i < c->pending.size() && i < upto; ++i) {
+        auto& p = c->pending[i];
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return e;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return e;
+        c->prof_ms[p.kind] += ms;
+        c->prof_n[p.kind] += 1;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pending.erase(c->pending.begin(), c->pending.begin() + i);
+    return cudaSuccess;
+}
+
+// Run one launch (or a group of launches) of kernel kind `kind`, bracketed by
+// events when profiling is on.
+template <typename F>
+cudaError_t timed(psatd_ctx* c, int kind, F&& launch) {
+    if (!c->prof_on) return launch();
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b, c->stream);
+    if (e != cudaSuccess) return e;
+    c->pending.push_back({a, b, kind});
+    if (c->pending.size() > 8192) return harvest(c, 4096);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t fft_axis(psatd_ctx* c, cplx<T>* data, int ncomp, int axis, int dir, int kind) {
+    const GridGeom g = geom(c);
+    const Tables<T> tb = tables<T>(c);
+    return timed(c, kind < 0 ? axis : kind, [&] {
+        return launch_fft_axis<T>(data, ncomp, g, tb, axis, dir, c->stream, &c->launches);
+    });
+}
+
+template <typename T>
+cudaError_t fft3d(psatd_ctx* c, cplx<T>* data, int ncomp, int dir, int kind = -1) {
+    cudaError_t e;
+    const int order_f[3] = {0, 1, 2}, order_i[3] = {2, 1, 0};
+    const int* order = dir < 0 ? order_f : order_i;
+    for (int q = 0; q < 3; ++q) {
+        e = fft_axis<T>(c, data, ncomp, order[q], dir, kind);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One spectral pass: forward x, y; fused z-forward / mode update / z-inverse;
+// inverse y, x.
+template <typename T>
+cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
+    const GridGeom g = geom(c);
+    const Tables<T> tb = tables<T>(c);
+    cplx<T>* f = static_cast<cplx<T>*>(c->fields);
+    cudaError_t e;
+    if ((e = fft_axis<T>(c, f, 6, 0, -1, -1)) != cudaSuccess) return e;
+    if ((e = fft_axis<T>(c, f, 6, 1, -1, -1)) != cudaSuccess) return e;
+    e = timed(c, PSATD_KERNEL_KSPACE, [&] {
+        return launch_kspace_z<T>(f, g, tb, mode, scale, c->stream, &c->launches);
+    });
+    if (e != cudaSuccess) return e;
+    if ((e = fft_axis<T>(c, f, 6, 1, +1, -1)) != cudaSuccess) return e;
+    if ((e = fft_axis<T>(c, f, 6, 0, +1, -1)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+double F_series(double t0) {
+    const double t2 = t0 * t0;
+    return t2 / 4 - t2 * t2 / 48 + t2 * t2 * t2 / 960;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* psatd_status_string(psatd_status s) {
+    switch (s) {
+        case PSATD_OK: return "PSATD_OK";
+        case PSATD_ERR_ARG: return "PSATD_ERR_ARG";
+        case PSATD_ERR_SIZE: return "PSATD_ERR_SIZE";
+        case PSATD_ERR_OOM: return "PSATD_ERR_OOM";
+        case PSATD_ERR_CUDA: return "PSATD_ERR_CUDA";
+        case PSATD_ERR_TIMEOUT: return "PSATD_ERR_TIMEOUT";
+        case PSATD_ERR_STATE: return "PSATD_ERR_STATE";
+    }
+    return "PSATD_ERR_UNKNOWN";
+}
+
+const char* psatd_last_error(const psatd_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+double psatd_d_min(double R0, double L, double theta) {
+    const double rmin = R0 - 0.5 * L, rmax = R0 + 0.5 * L;
+    const double s = rmin * std::sin(theta);
+    return -rmin * std::cos(theta) + std::sqrt(rmax * rmax - s * s);
+}
+
+psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mapping, double dt,
+                             int precision, void* cuda_stream, int flags, psatd_ctx** out) {
+    if (!grid || !out) return fail(nullptr, PSATD_ERR_ARG, "NULL grid or out pointer");
+    *out = nullptr;
+    if (precision != 32 && precision != 64) return fail(nullptr, PSATD_ERR_ARG, "precision must be 32 or 64");
+    const int Ns[3] = {grid->Nx, grid->Ny, grid->Nz};
+    for (int a = 0; a < 3; ++a) {
+        AxisPlan p;
+        if (Ns[a] < 1 || Ns[a] > kMaxN || !make_plan(Ns[a], &p)) {
+            char b[160];
+            snprintf(b, sizeof b, "axis %d: N=%d must be in 1..%d with prime factors 2, 3, 5 only", a, Ns[a], kMaxN);
+            return fail(nullptr, PSATD_ERR_SIZE, b);
+        }
+    }
+    const double ds[3] = {grid->dx, grid->dy, grid->dz};
+    for (double d : ds)
+        if (!(is_finite(d) && d > 0)) return fail(nullptr, PSATD_ERR_ARG, "dx, dy, dz must be finite and > 0");
+    if (!(is_finite(grid->c) && grid->c > 0)) return fail(nullptr, PSATD_ERR_ARG, "c must be finite and > 0");
+    if (!is_finite(grid->x_min) || !is_finite(grid->y_min) || !is_finite(grid->z_min))
+        return fail(nullptr, PSATD_ERR_ARG, "x_min, y_min, z_min must be finite");
+    if (!is_finite(dt)) return fail(nullptr, PSATD_ERR_ARG, "dt must be finite");
+    if (mapping && !(is_finite(mapping->R0) && is_finite(mapping->L) && mapping->L >= 0))
+        return fail(nullptr, PSATD_ERR_ARG, "mapping R0, L must be finite, L >= 0");
+
+    psatd_ctx* c = new (std::nothrow) psatd_ctx();
+    if (!c) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
+    c->grid = *grid;
+    if (mapping) c->mapping = *mapping;
+    c->dt = dt;
+    c->prec = precision;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int a = 0; a < 3; ++a) make_plan(Ns[a], &c->plan[a]);
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    psatd_status st = PSATD_OK;
+    if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGetDevice");
+    if (st == PSATD_OK) st = precision == 64 ? upload_axis_tables<double>(c) : upload_axis_tables<float>(c);
+    if (st == PSATD_OK) st = set_coef(c, dt);
+    if (st == PSATD_OK && !(flags & PSATD_FLAG_NO_FIELD_ALLOC)) {
+        const size_t bytes = 6 * n_cells(*grid) * cplx_size(precision);
+        e = cudaMalloc(&c->fields, bytes);
+        if (e != cudaSuccess) {
+            c->fields = nullptr;
+            st = cuda_fail(c, e, "cudaMalloc(fields)");
+        } else {
+            c->field_bytes = bytes;
+            c->own_fields = true;
+            e = cudaMemsetAsync(c->fields, 0, bytes, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMemset(fields)");
+        }
+    }
+    if (st != PSATD_OK) {
+        g_create_error = c->err;
+        psatd_destroy(c);
+        return st;
+    }
+    *out = c;
+    return PSATD_OK;
+}
+
+void psatd_destroy(psatd_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->own_fields && c->fields) cudaFree(c->fields);
+    for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
+    free_buf(c->coef);
+    free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
+    free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
+    free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
+    for (auto& p : c->pending) { c->ev_pool.push_back(p.a); c->ev_pool.push_back(p.b); }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+psatd_status psatd_set_dt(psatd_ctx* c, double dt) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    if (!is_finite(dt)) return fail(c, PSATD_ERR_ARG, "dt must be finite");
+    st = set_coef(c, dt);
+    if (st == PSATD_OK) c->dt = dt;
+    return st;
+}
+
+psatd_status psatd_bind_fields(psatd_ctx* c, void* dev_ptr, size_t bytes) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    const size_t need = 6 * n_cells(c->grid) * cplx_size(c->prec);
+    if (!dev_ptr) return fail(c, PSATD_ERR_ARG, "NULL field pointer");
+    if (bytes < need) return fail(c, PSATD_ERR_ARG, "field storage too small");
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0) return fail(c, PSATD_ERR_ARG, "field storage must be 256-byte aligned");
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, dev_ptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaPointerGetAttributes");
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(c, PSATD_ERR_ARG, "field storage must be device memory");
+    if (c->own_fields && c->fields) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->fields);
+    }
+    c->fields = dev_ptr;
+    c->field_bytes = bytes;
+    c->own_fields = false;
+    return PSATD_OK;
+}
+
+psatd_status psatd_fields(psatd_ctx* c, void** dev_ptr, size_t* bytes) {
+    if (!c || !dev_ptr) return fail(c, PSATD_ERR_ARG, "NULL argument");
+    *dev_ptr = c->fields;
+    if (bytes) *bytes = c->field_bytes;
+    return PSATD_OK;
+}
+
+static psatd_status copy_field(psatd_ctx* c, int comp, void* dst, const void* src, int on_device,
+                               bool to_lib) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (comp < -1 || comp > 5) return fail(c, PSATD_ERR_ARG, "comp must be -1..5");
+    if (!(to_lib ? src : dst)) return fail(c, PSATD_ERR_ARG, "NULL buffer");
+    const size_t per = n_cells(c->grid) * cplx_size(c->prec);
+    const size_t bytes = comp < 0 ? 6 * per : per;
+    char* lib = static_cast<char*>(c->fields) + (comp < 0 ? 0 : comp * per);
+    cudaMemcpyKind kind;
+    if (to_lib) kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    else kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(c, cudaMemcpyAsync(to_lib ? lib : dst, to_lib ? src : lib, bytes, kind, c->stream));
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    return PSATD_OK;
+}
+
+psatd_status psatd_set_field(psatd_ctx* c, int comp, const void* src, int src_on_device) {
+    return copy_field(c, comp, nullptr, src, src_on_device, true);
+}
+
+psatd_status psatd_get_field(psatd_ctx* c, int comp, void* dst, int dst_on_device) {
+    return copy_field(c, comp, dst, nullptr, dst_on_device, false);
+}
+
+psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (!p) return fail(c, PSATD_ERR_ARG, "NULL pulse");
+    if (p->kind != PSATD_PULSE_FLAT_TOP && p->kind != PSATD_PULSE_GAUSSIAN)
+        return fail(c, PSATD_ERR_ARG, "unknown pulse kind");
+    const double vals[8] = {p->lambda, p->theta, p->eps, p->P0, p->n_cycles, p->cep, p->ellipticity, p->pol_angle};
+    for (double v : vals)
+        if (!is_finite(v)) return fail(c, PSATD_ERR_ARG, "pulse parameters must be finite");
+    if (!(p->lambda > 0) || !(p->theta > 0) || p->eps < 0 || p->P0 < 0)
+        return fail(c, PSATD_ERR_ARG, "need lambda > 0, theta > 0, eps >= 0, P0 >= 0");
+    if (p->kind == PSATD_PULSE_GAUSSIAN && !(p->n_cycles > 0))
+        return fail(c, PSATD_ERR_ARG, "Gaussian pulse needs n_cycles > 0");
+    if (!(c->mapping.R0 > 0) || !(c->mapping.L > 0))
+        return fail(c, PSATD_ERR_ARG, "mapping R0 and L must be > 0 for a pulse");
+    if (p->kind == PSATD_PULSE_FLAT_TOP && !(std::cos(p->theta) < 1.0))
+        return fail(c, PSATD_ERR_ARG, "flat-top theta too small");
+
+    PulseParams pp;
+    pp.kind = p->kind; pp.div_project = p->div_project;
+    pp.lambda = p->lambda; pp.theta = p->theta; pp.eps = p->eps; pp.P0 = p->P0;
+    pp.n_cycles = p->n_cycles; pp.cep = p->cep; pp.ellipticity = p->ellipticity;
+    pp.pol_angle = p->pol_angle;
+    if (p->kind == PSATD_PULSE_FLAT_TOP)
+        pp.amp = std::sqrt(4.0 * p->P0 / (c->grid.c * (1.0 - std::cos(p->theta))));           // Eq. 9
+    else
+        pp.amp = std::sqrt(4.0 * p->P0 / (c->grid.c * c->mapping.R0 * c->mapping.R0 * F_series(p->theta)));
+
+    // replicas m whose copy x~ + m D can meet the shell |R| <= R_max
+    const double D = c->grid.Nx * c->grid.dx;
+    const double rmax = c->mapping.R0 + 0.5 * c->mapping.L;
+    const int m_lo = (int)std::floor((-rmax - (c->grid.x_min + D)) / D) - 1;
+    const int m_hi = (int)std::ceil((rmax - c->grid.x_min) / D) + 1;
+    if (m_hi - m_lo > 100000) return fail(c, PSATD_ERR_ARG, "shell spans too many replicas of the layer");
+
+    ShellGeom sh{c->mapping.R0, c->mapping.L};
+    const GridGeom g = geom(c);
+    cudaError_t e = timed(c, PSATD_KERNEL_INIT, [&] {
+        return c->prec == 64
+            ? launch_init_pulse<double>(static_cast<cplx<double>*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches)
+            : launch_init_pulse<float>(static_cast<cplx<float>*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "init_pulse launch");
+    if (p->div_project) {
+        const double scale = 1.0 / (double)n_cells(c->grid);
+        e = c->prec == 64 ? spectral_pass<double>(c, KS_PROJECT, scale) : spectral_pass<float>(c, KS_PROJECT, scale);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection launch");
+    }
+    c->t = 0.0;
+    return PSATD_OK;
+}
+
+psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (n_steps < 0) return fail(c, PSATD_ERR_ARG, "n_steps must be >= 0");
+    for (int s = 0; s < n_steps; ++s) {
+        cudaError_t e = c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0)
+                                      : spectral_pass<float>(c, KS_ROTATE, 0.0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
+        c->t += c->dt;
+    }
+    return PSATD_OK;
+}
+
+psatd_status psatd_fft(psatd_ctx* c, int direction) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (direction != PSATD_FORWARD && direction != PSATD_INVERSE)
+        return fail(c, PSATD_ERR_ARG, "direction must be PSATD_FORWARD or PSATD_INVERSE");
+    cudaError_t e = c->prec == 64 ? fft3d<double>(c, static_cast<cplx<double>*>(c->fields), 6, direction)
+                                  : fft3d<float>(c, static_cast<cplx<float>*>(c->fields), 6, direction);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fft launch");
+    return PSATD_OK;
+}
+
+psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int nz, double y0, double y1,
+                                      double z0, double z1, int comp_mask, void* dst, int dst_on_device) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
+    if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
+    if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
+        return fail(c, PSATD_ERR_ARG, "plane coordinates must be finite");
+    if (comp_mask <= 0 || comp_mask > 63) return fail(c, PSATD_ERR_ARG, "comp_mask must select 1..6 components");
+    int comps[6], nc = 0;
+    for (int a = 0; a < 6; ++a)
+        if (comp_mask & (1 << a)) comps[nc++] = a;
+    const psatd_grid& g = c->grid;
+    CK(c, ensure_buf(c->samp_wx, g.Nx * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_wy, (size_t)ny * g.Ny * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_wz, (size_t)nz * g.Nz * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_g, (size_t)nc * g.Nz * g.Ny * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_h, (size_t)nc * g.Nz * ny * sizeof(double2)));
+    const size_t out_bytes = (size_t)nc * nz * ny * cplx_size(c->prec);
+    void* out = dst;
+    if (!dst_on_device) {
+        CK(c, ensure_buf(c->samp_out, out_bytes));
+        out = c->samp_out.p;
+    }
+    SampleScratch sc{static_cast<double2*>(c->samp_wx.p), static_cast<double2*>(c->samp_wy.p),
+                     static_cast<double2*>(c->samp_wz.p), static_cast<double2*>(c->samp_g.p),
+                     static_cast<double2*>(c->samp_h.p)};
+    ShellGeom sh{c->mapping.R0, c->mapping.L};
+    const GridGeom gg = geom(c);
+    cudaError_t e = timed(c, PSATD_KERNEL_SAMPLE, [&] {
+        return c->prec == 64
+            ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches)
+            : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "sample launch");
+    if (!dst_on_device) {
+        CK(c, cudaMemcpyAsync(dst, out, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return PSATD_OK;
+}
+
+psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
+    psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (!out) return fail(c, PSATD_ERR_ARG, "NULL out");
+    const size_t n = n_cells(c->grid);
+    const size_t es = cplx_size(c->prec);
+    CK(c, ensure_buf(c->diag_spec, 3 * n * es));
+    CK(c, ensure_buf(c->diag_partial, (size_t)kDiagBlocks * 2 * sizeof(double)));
+    CK(c, ensure_buf(c->diag_out, 8 * sizeof(double)));
+    double* partial = static_cast<double*>(c->diag_partial.p);
+    double* res = static_cast<double*>(c->diag_out.p);
+    double host[6];
+    const GridGeom g = geom(c);
+    cudaError_t e = timed(c, PSATD_KERNEL_DIAG, [&] {
+        cudaError_t r = c->prec == 64
+            ? launch_energy<double>(static_cast<const cplx<double>*>(c->fields), n, partial, kDiagBlocks, c->stream, &c->launches)
+            : launch_energy<float>(static_cast<const cplx<float>*>(c->fields), n, partial, kDiagBlocks, c->stream, &c->launches);
+        if (r != cudaSuccess) return r;
+        return launch_reduce_final(partial, kDiagBlocks, 2, 2, res, c->stream, &c->launches);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy launch");
+    for (int half = 0; half < 2; ++half) {
+        const char* src = static_cast<const char*>(c->fields) + (size_t)3 * half * n * es;
+        CK(c, cudaMemcpyAsync(c->diag_spec.p, src, 3 * n * es, cudaMemcpyDeviceToDevice, c->stream));
+        if (c->prec == 64) e = fft3d<double>(c, static_cast<cplx<double>*>(c->diag_spec.p), 3, -1, PSATD_KERNEL_DIAG);
+        else e = fft3d<float>(c, static_cast<cplx<float>*>(c->diag_spec.p), 3, -1, PSATD_KERNEL_DIAG);
+        if (e != cudaSuccess) return cuda_fail(c, e, "divergence fft launch");
+        e = timed(c, PSATD_KERNEL_DIAG, [&] {
+            cudaError_t r = c->prec == 64
+                ? launch_divergence<double>(static_cast<const cplx<double>*>(c->diag_spec.p), g, tables<double>(c), partial, kDiagBlocks, c->stream, &c->launches)
+                : launch_divergence<float>(static_cast<const cplx<float>*>(c->diag_spec.p), g, tables<float>(c), partial, kDiagBlocks, c->stream, &c->launches);
+            if (r != cudaSuccess) return r;
+            return launch_reduce_final(partial, kDiagBlocks, 2, 0, res + 2 + 2 * half, c->stream, &c->launches);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "divergence launch");
+    }
+    CK(c, cudaMemcpyAsync(host, res, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    out->energy_E = host[0];
+    out->energy_B = host[1];
+    out->energy = host[0] + host[1];
+    out->max_div_E = host[2];
+    out->max_E_hat = host[3];
+    out->max_div_B = host[4];
+    out->max_B_hat = host[5];
+    return PSATD_OK;
+}
+
+double psatd_time(const psatd_ctx* c) { return c ? c->t : 0.0; }
+
+psatd_status psatd_set_time(psatd_ctx* c, double t) {
+    if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
+    if (!is_finite(t)) return fail(c, PSATD_ERR_ARG, "t must be finite");
+    c->t = t;
+    return PSATD_OK;
+}
+
+psatd_status psatd_synchronize(psatd_ctx* c) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PSATD_OK;
+}
+
+long long psatd_launch_count(const psatd_ctx* c) { return c ? c->launches : 0; }
+
+psatd_status psatd_profile_enable(psatd_ctx* c, int enable) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    CK(c, harvest(c, c->pending.size()));
+    for (int k = 0; k < PSATD_KERNEL_KINDS; ++k) { c->prof_ms[k] = 0.0; c->prof_n[k] = 0; }
+    c->prof_on = enable != 0;
+    return PSATD_OK;
+}
+
+psatd_status psatd_profile_read(psatd_ctx* c, int kind, double* total_ms, long long* launches) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    if (kind < 0 || kind >= PSATD_KERNEL_KINDS) return fail(c, PSATD_ERR_ARG, "unknown kernel kind");
+    CK(c, harvest(c, c->pending.size()));
+    if (total_ms) *total_ms = c->prof_ms[kind];
+    if (launches) *launches = c->prof_n[kind];
+    return PSATD_OK;
+}
+
+const char* psatd_kernel_name(int kind) {
+    static const char* names[PSATD_KERNEL_KINDS] = {"fft_x", "fft_y", "fft_z", "kspace_z",
+                                                    "init_pulse", "sample_plane", "diagnostics",
+                                                    "plane_xy"};
+    return (kind >= 0 && kind < PSATD_KERNEL_KINDS) ? names[kind] : "unknown";
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Focal-plane sampling (Sec. 2.3, Eq. 13-16).
+//
+// The field at a physical point R = (x_p, y, z) is u~(T(R)) * I_S(t)(R), with T
+// of Eq. 13 and u~ the exact trigonometric interpolant of the periodic grid
+// field: u~(r) = (1/N) sum_m F(m) exp(i k_m . (r - r_min)).  Substituting the
+// forward DFT gives the separable form
+//     u~(r) = sum_{i,j,l} w_x(x - x_i) w_y(y - y_j) w_z(z - z_l) f_{l j i},
+//     w_N(s) = (1/N) sum_m exp(i 2 pi m s / (N d)),  m = -floor(N/2) .. ceil(N/2)-1,
+// and the geometric sum closes to
+//     w_N(s) = exp(i (m_lo + (N-1)/2) phi) sin(N phi / 2) / (N sin(phi / 2)),
+//     phi = 2 pi s / (N d)   (w = 1 at phi = 0; w is N d-periodic in s).
+// The three contractions (x, then y, then z) run in float64.
+#include "common.cuh"
+
+namespace psatd {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ double2 dirichlet_weight(double s, int N, double d) {
+    double u = s / (N * d);
+    u -= floor(u + 0.5);                       // u in [-1/2, 1/2)
+    if (u == 0.0) return make_double2(1.0, 0.0);
+    const double phi = 2.0 * kPi * u;
+    const double m_c = (double)(-(N / 2)) + 0.5 * (N - 1);
+    const double ratio = sin(0.5 * N * phi) / (N * sin(0.5 * phi));
+    return make_double2(ratio * cos(m_c * phi), ratio * sin(m_c * phi));
+}
+
+__device__ __forceinline__ double cut_out_indicator(double x, double y, double z, double t,
+                                                    const ShellGeom& sh, double c) {
+    // Eq. 15-16; the third case reads "R > r(t)" (the printed "R > l(t)" would
+    // remove the focus itself, since l(t) <= 0 there).
+    const double R = sqrt(x * x + y * y + z * z);
+    const double Rmin = sh.R0 - 0.5 * sh.L, Rmax = sh.R0 + 0.5 * sh.L;
+    const double l = -Rmax + c * t, r = -Rmin + c * t;
+    bool zero = false;
+    if (r < 0) zero = zero || (R >= -l) || (R < -r) || (x > 0);
+    if (l <= 0 && r >= 0) {
+        zero = zero || ((x < 0) && (R > sh.L));
+        zero = zero || ((x >= 0) && (R > r));
+    }
+    if (l > 0) zero = zero || (R <= l) || (R > r) || (x < 0);
+    return zero ? 0.0 : 1.0;
+}
+
+__global__ void weights_kernel(GridGeom g, double x_phys, int ny, int nz, double y0, double y1,
+                               double z0, double z1, double2* wx, double2* wy, double2* wz) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nwx = g.Nx, nwy = ny * g.Ny, nwz = nz * g.Nz;
+    const double D = g.Nx * g.dx;
+    if (tid < nwx) {
+        double q = (x_phys - g.x_min) / D;
+        const double xt = g.x_min + D * (q - floor(q));              // Eq. 13
+        wx[tid] = dirichlet_weight(xt - (g.x_min + tid * g.dx), g.Nx, g.dx);
+    } else if (tid < nwx + nwy) {
+        const int e = tid - nwx, p = e / g.Ny, j = e - p * g.Ny;
+        const double y = y0 + (y1 - y0) * p / ny;
+        wy[e] = dirichlet_weight(y - (g.y_min + j * g.dy), g.Ny, g.dy);
+    } else if (tid < nwx + nwy + nwz) {
+        const int e = tid - nwx - nwy, q = e / g.Nz, l = e - q * g.Nz;
+        const double z = z0 + (z1 - z0) * q / nz;
+        wz[e] = dirichlet_weight(z - (g.z_min + l * g.dz), g.Nz, g.dz);
+    }
+}
+
+struct CompList { int c[6]; };
+
+// g[a][l][j] = sum_i wx[i] f[c_a][l][j][i]; one warp per (a, l, j) row.
+template <typename T>
+__global__ void contract_x_kernel(const cplx<T>* __restrict__ f, GridGeom g, CompList cl, int ncomp,
+                                  const double2* __restrict__ wx, double2* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long rows = (long long)ncomp * g.Nz * g.Ny;
+    if (warp >= rows) return;
+    const int a = (int)(warp / ((long long)g.Nz * g.Ny));
+    const long long rl = warp - (long long)a * g.Nz * g.Ny;
+    const cplx<T>* row = f + (size_t)cl.c[a] * g.Nx * g.Ny * g.Nz + (size_t)rl * g.Nx;
+    double re = 0.0, im = 0.0;
+    for (int i = lane; i < g.Nx; i += 32) {
+        const cplx<T> v = row[i];
+        const double2 w = wx[i];
+        re += w.x * (double)v.x - w.y * (double)v.y;
+        im += w.x * (double)v.y + w.y * (double)v.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) out[warp] = make_double2(re, im);
+}
+
+// h[a][l][p] = sum_j wy[p][j] g[a][l][j]
+__global__ void contract_y_kernel(const double2* __restrict__ gin, GridGeom g, int ncomp, int ny,
+                                  const double2* __restrict__ wy, double2* __restrict__ h) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)ncomp * g.Nz * ny) return;
+    const int p = (int)(tid % ny);
+    const long long al = tid / ny;                 // a * Nz + l
+    const double2* gr = gin + (size_t)al * g.Ny;
+    const double2* w = wy + (size_t)p * g.Ny;
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < g.Ny; ++j) {
+        const double2 a = gr[j], b = w[j];
+        re += b.x * a.x - b.y * a.y;
+        im += b.x * a.y + b.y * a.x;
+    }
+    h[tid] = make_double2(re, im);
+}
+
+// out[a][q][p] = I_S(x_p, y_p, z_q, t) * sum_l wz[q][l] h[a][l][p]
+template <typename T>
+__global__ void contract_z_kernel(const double2* __restrict__ h, GridGeom g, ShellGeom sh, int ncomp,
+                                  int ny, int nz, double x_phys, double y0, double y1, double z0,
+                                  double z1, double t, const double2* __restrict__ wz,
+                                  cplx<T>* __restrict__ out) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)ncomp * nz * ny) return;
+    const int p = (int)(tid % ny);
+    const long long r = tid / ny;
+    const int q = (int)(r % nz);
+    const int a = (int)(r / nz);
+    const double2* w = wz + (size_t)q * g.Nz;
+    const double2* hc = h + (size_t)a * g.Nz * ny + p;
+    double re = 0.0, im = 0.0;
+    for (int l = 0; l < g.Nz; ++l) {
+        const double2 v = hc[(size_t)l * ny], b = w[l];
+        re += b.x * v.x - b.y * v.y;
+        im += b.x * v.y + b.y * v.x;
+    }
+    const double y = y0 + (y1 - y0) * p / ny;
+    const double z = z0 + (z1 - z0) * q / nz;
+    const double m = cut_out_indicator(x_phys, y, z, t, sh, g.c);
+    out[tid] = mk<T>((T)(re * m), (T)(im * m));
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const ShellGeom& sh,
+                                double x_phys, int ny, int nz, double y0, double y1, double z0,
+                                double z1, double t, const int* comps, int ncomp,
+                                const SampleScratch& sc, cplx<T>* out, cudaStream_t s,
+                                long long* nlaunch) {
+    CompList cl;
+    for (int a = 0; a < 6; ++a) cl.c[a] = a < ncomp ? comps[a] : 0;
+    const int nw = g.Nx + ny * g.Ny + nz * g.Nz;
+    weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
+    const long long rows = (long long)ncomp * g.Nz * g.Ny;
+    contract_x_kernel<T><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(data, g, cl, ncomp, sc.wx, sc.g);
+    const long long nh = (long long)ncomp * g.Nz * ny;
+    contract_y_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(sc.g, g, ncomp, ny, sc.wy, sc.h);
+    const long long no = (long long)ncomp * nz * ny;
+    contract_z_kernel<T><<<(unsigned)((no + 255) / 256), 256, 0, s>>>(sc.h, g, sh, ncomp, ny, nz, x_phys,
+                                                                      y0, y1, z0, z1, t, sc.wz, out);
+    if (nlaunch) *nlaunch += 4;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sample_plane<float>(const cplx<float>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<float>*, cudaStream_t, long long*);
+template cudaError_t launch_sample_plane<double>(const cplx<double>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<double>*, cudaStream_t, long long*);
+
+}  // namespace psatd

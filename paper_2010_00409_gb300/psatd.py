@@ -1,0 +1,256 @@
+"""Python binding of the C ABI in include/psatd.h (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA library libpsatd.so.  Importing this
+module loads the library and raises if it is missing: there is no fallback.
+Device memory and streams come from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsatd.so")
+
+OK = 0
+ERR_ARG, ERR_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6
+FLAT_TOP, GAUSSIAN = 0, 1
+FORWARD, INVERSE = -1, +1
+FLAG_NO_FIELD_ALLOC = 1
+
+# every symbol include/psatd.h declares
+EXPORTS = (
+    "psatd_init_grid", "psatd_destroy", "psatd_set_dt", "psatd_bind_fields", "psatd_fields",
+    "psatd_set_field", "psatd_get_field", "psatd_init_pulse", "psatd_advance", "psatd_fft",
+    "psatd_sample_focal_plane", "psatd_diagnostics", "psatd_time", "psatd_set_time",
+    "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
+    "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
+)
+
+KERNEL_KINDS = ("fft_x", "fft_y", "fft_z", "kspace_z", "init_pulse", "sample_plane", "diagnostics",
+                "plane_xy")
+
+
+class PsatdGrid(C.Structure):
+    _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("x_min", C.c_double), ("y_min", C.c_double), ("z_min", C.c_double),
+                ("c", C.c_double)]
+
+
+class PsatdMapping(C.Structure):
+    _fields_ = [("R0", C.c_double), ("L", C.c_double)]
+
+
+class PsatdPulse(C.Structure):
+    _fields_ = [("kind", C.c_int), ("div_project", C.c_int),
+                ("lambda_", C.c_double), ("theta", C.c_double), ("eps", C.c_double),
+                ("P0", C.c_double), ("n_cycles", C.c_double), ("cep", C.c_double),
+                ("ellipticity", C.c_double), ("pol_angle", C.c_double)]
+
+
+class PsatdDiag(C.Structure):
+    _fields_ = [("energy", C.c_double), ("energy_E", C.c_double), ("energy_B", C.c_double),
+                ("max_div_E", C.c_double), ("max_div_B", C.c_double),
+                ("max_E_hat", C.c_double), ("max_B_hat", C.c_double)]
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError("libpsatd.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "psatd_init_grid": (C.c_int, [C.POINTER(PsatdGrid), C.POINTER(PsatdMapping), C.c_double, C.c_int, P, C.c_int, C.POINTER(P)]),
+        "psatd_destroy": (None, [P]),
+        "psatd_set_dt": (C.c_int, [P, C.c_double]),
+        "psatd_bind_fields": (C.c_int, [P, P, C.c_size_t]),
+        "psatd_fields": (C.c_int, [P, C.POINTER(P), C.POINTER(C.c_size_t)]),
+        "psatd_set_field": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "psatd_get_field": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "psatd_init_pulse": (C.c_int, [P, C.POINTER(PsatdPulse)]),
+        "psatd_advance": (C.c_int, [P, C.c_int]),
+        "psatd_fft": (C.c_int, [P, C.c_int]),
+        "psatd_sample_focal_plane": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double,
+                                               C.c_double, C.c_double, C.c_int, P, C.c_int]),
+        "psatd_diagnostics": (C.c_int, [P, C.POINTER(PsatdDiag)]),
+        "psatd_time": (C.c_double, [P]),
+        "psatd_set_time": (C.c_int, [P, C.c_double]),
+        "psatd_synchronize": (C.c_int, [P]),
+        "psatd_d_min": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+        "psatd_last_error": (C.c_char_p, [P]),
+        "psatd_status_string": (C.c_char_p, [C.c_int]),
+        "psatd_launch_count": (C.c_longlong, [P]),
+        "psatd_profile_enable": (C.c_int, [P, C.c_int]),
+        "psatd_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+        "psatd_kernel_name": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class PsatdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (lib().psatd_status_string(status).decode(), msg))
+        self.status = status
+
+
+def _check(status: int, ctx_ptr=None):
+    if status != OK:
+        raise PsatdError(status, lib().psatd_last_error(ctx_ptr).decode())
+
+
+def d_min(R0: float, L: float, theta: float) -> float:
+    """Eq. 12 through the library."""
+    return lib().psatd_d_min(R0, L, theta)
+
+
+def make_grid(g) -> PsatdGrid:
+    return PsatdGrid(g.Nx, g.Ny, g.Nz, g.dx, g.dy, g.dz, g.x_min, g.y_min, g.z_min, g.c)
+
+
+def make_pulse(p) -> PsatdPulse:
+    return PsatdPulse(p.kind, p.div_project, p.lam, p.theta, p.eps, p.P0, p.n_cycles, p.cep,
+                      p.ellipticity, p.pol_angle)
+
+
+class Context:
+    """One periodic box on the current CUDA device; fields are a torch tensor
+    [6, Nz, Ny, Nx] (complex64 or complex128) bound to the library."""
+
+    def __init__(self, grid, mapping=None, dt: float = 0.0, precision: int = 64, stream=None,
+                 fields=None):
+        import torch
+        self._torch = torch
+        self.grid = grid
+        self.precision = precision
+        self.dtype = torch.complex128 if precision == 64 else torch.complex64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        m = PsatdMapping(mapping.R0, mapping.L) if mapping is not None else None
+        ptr = C.c_void_p()
+        st = lib().psatd_init_grid(C.byref(make_grid(grid)), C.byref(m) if m is not None else None, dt,
+                                   precision, C.c_void_p(self.stream.cuda_stream), FLAG_NO_FIELD_ALLOC,
+                                   C.byref(ptr))
+        _check(st, None)
+        self._ptr = ptr
+        if fields is None:
+            fields = torch.zeros((6, grid.Nz, grid.Ny, grid.Nx), dtype=self.dtype, device=dev)
+        assert fields.dtype == self.dtype and fields.is_contiguous() and fields.is_cuda
+        self.fields = fields
+        _check(lib().psatd_bind_fields(self._ptr, C.c_void_p(fields.data_ptr()),
+                                       fields.numel() * fields.element_size()), self._ptr)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_ptr", None) is not None and self._ptr.value:
+            lib().psatd_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def set_dt(self, dt: float):
+        _check(lib().psatd_set_dt(self._ptr, dt), self._ptr)
+
+    def set_field(self, comp: int, src):
+        """src: numpy array (host) or torch tensor (device), layout of the storage."""
+        if isinstance(src, np.ndarray):
+            want = np.complex128 if self.precision == 64 else np.complex64
+            a = np.ascontiguousarray(src, dtype=want)
+            _check(lib().psatd_set_field(self._ptr, comp, a.ctypes.data_as(C.c_void_p), 0), self._ptr)
+        else:
+            t = src.to(self.dtype).contiguous()
+            _check(lib().psatd_set_field(self._ptr, comp, C.c_void_p(t.data_ptr()), 1), self._ptr)
+
+    def set_fields(self, src):
+        self.set_field(-1, src)
+
+    def get_field(self, comp: int = -1) -> np.ndarray:
+        want = np.complex128 if self.precision == 64 else np.complex64
+        shape = (self.grid.Nz, self.grid.Ny, self.grid.Nx)
+        out = np.empty(((6,) if comp < 0 else ()) + shape, dtype=want)
+        _check(lib().psatd_get_field(self._ptr, comp, out.ctypes.data_as(C.c_void_p), 0), self._ptr)
+        return out
+
+    def init_pulse(self, pulse):
+        _check(lib().psatd_init_pulse(self._ptr, C.byref(make_pulse(pulse))), self._ptr)
+
+    def advance(self, n: int):
+        _check(lib().psatd_advance(self._ptr, n), self._ptr)
+
+    def fft(self, direction: int):
+        _check(lib().psatd_fft(self._ptr, direction), self._ptr)
+
+    def sample_focal_plane(self, x_phys, ny, nz, y0, y1, z0, z1, comps=(0, 1, 2), out=None):
+        mask = 0
+        for c in comps:
+            mask |= 1 << c
+        nc = bin(mask).count("1")
+        if out is None:
+            want = np.complex128 if self.precision == 64 else np.complex64
+            out = np.empty((nc, nz, ny), dtype=want)
+            _check(lib().psatd_sample_focal_plane(self._ptr, x_phys, ny, nz, y0, y1, z0, z1, mask,
+                                                  out.ctypes.data_as(C.c_void_p), 0), self._ptr)
+            return out
+        assert out.dtype == self.dtype and out.is_cuda and out.numel() >= nc * ny * nz
+        _check(lib().psatd_sample_focal_plane(self._ptr, x_phys, ny, nz, y0, y1, z0, z1, mask,
+                                              C.c_void_p(out.data_ptr()), 1), self._ptr)
+        return out
+
+    def diagnostics(self) -> dict:
+        d = PsatdDiag()
+        _check(lib().psatd_diagnostics(self._ptr, C.byref(d)), self._ptr)
+        return {k: getattr(d, k) for k, _ in PsatdDiag._fields_}
+
+    @property
+    def time(self) -> float:
+        return lib().psatd_time(self._ptr)
+
+    def set_time(self, t: float):
+        _check(lib().psatd_set_time(self._ptr, t), self._ptr)
+
+    def synchronize(self):
+        _check(lib().psatd_synchronize(self._ptr), self._ptr)
+
+    @property
+    def launch_count(self) -> int:
+        return lib().psatd_launch_count(self._ptr)
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().psatd_profile_enable(self._ptr, 1 if on else 0), self._ptr)
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, timed launches)} since profiling was enabled."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            ms, n = C.c_double(), C.c_longlong()
+            _check(lib().psatd_profile_read(self._ptr, k, C.byref(ms), C.byref(n)), self._ptr)
+            if n.value:
+                out[name] = (ms.value, n.value)
+        return out
