@@ -183,6 +183,13 @@ const char* psatd_status_string(psatd_status s);
 /* Number of kernel launches the context has issued since creation. */
 long long psatd_launch_count(const psatd_ctx* ctx);
 
+/* Kernel selection: AUTO uses the register-resident kernels where the axis
+ * length has one (64, 128, 256, 512) and the generic shared-memory Stockham
+ * kernels elsewhere; GENERIC forces the latter everywhere.  Both compute the
+ * same transform; the default is AUTO. */
+enum { PSATD_PATH_AUTO = 0, PSATD_PATH_GENERIC = 1 };
+psatd_status psatd_set_kernel_path(psatd_ctx* ctx, int path);
+
 /* Kernel kinds for per-kernel timing. */
 enum {
     PSATD_KERNEL_FFT_X = 0,      /* generic FFT along x */

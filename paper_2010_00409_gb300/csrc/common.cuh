@@ -89,6 +89,14 @@ template <typename T>
 cudaError_t launch_fft_axis(cplx<T>* data, int ncomp, const GridGeom& g, const Tables<T>& tb,
                             int axis, int dir, cudaStream_t s, long long* nlaunch);
 
+// Register-resident variants; cudaErrorNotSupported (nothing launched) when the
+// axis length or layout has no fast kernel.
+template <typename T>
+cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, const Tables<T>& tb,
+                                 int axis, int dir, cudaStream_t s);
+template <typename T>
+cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
+
 // Fused z-forward FFT, per-mode update, z-inverse FFT over all six components.
 template <typename T>
 cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode,

@@ -1,0 +1,351 @@
+// Fast FFT kernels for axis lengths N = N1 * N2 with a register plan
+// (see fft_reg.cuh): each pencil lives in the registers of N2 threads, goes
+// through one shared-memory exchange per transform, and is loaded and stored
+// straight from/to global memory with coalesced accesses.
+//
+//  fft_rows_kernel     x axis: one row per group of N2 threads.
+//  fft_cols_kernel     y or z axis: W consecutive x-columns x N2 threads.
+//  kspace_cols_kernel  the fused k-space pass of one PSATD step (Sec. 2.1,
+//                      Eq. 3-4): forward z transform of all six components of
+//                      W columns, the per-mode update in registers, inverse z
+//                      transform, one read and one write of the field.
+#include "fft_reg.cuh"
+
+namespace psatd {
+
+namespace {
+
+// exchange helpers with an explicit layout: element (k1, j) at k1*RS + j*ES
+template <typename T, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xscatter(const cplx<T> (&v)[N1], cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        sc[k1 * RS + j * ES] = v[k1];
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xgather_fwd(cplx<T> (&v)[N1], const cplx<T>* sc, int t) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        const cplx<T>* row = sc + (t + N2 * q) * RS;
+        static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value * ES]; });
+        reg_dft<T, S, N2>(w);
+        static_for<0, N2>([&](auto kc) { v[q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xscatter_inv(cplx<T> (&v)[N1], cplx<T>* sc, int t,
+                                             const cplx<T>* __restrict__ tw) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        static_for<0, N2>([&](auto kc) { w[decltype(kc)::value] = v[q * N2 + decltype(kc)::value]; });
+        reg_dft<T, S, N2>(w);
+        const int k1 = t + N2 * q;
+        cplx<T>* row = sc + k1 * RS;
+        static_for<0, N2>([&](auto nc) {
+            constexpr int n2 = decltype(nc)::value;
+            row[n2 * ES] = (n2 == 0) ? w[n2] : (k1 == 0 ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1)));
+        });
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xgather_inv(cplx<T> (&v)[N1], const cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        v[k1] = sc[k1 * RS + j * ES];
+    });
+    reg_dft<T, S, N1>(v);
+}
+
+// --------------------------------------------------------------------------- x
+// S = -1: natural order in (input layout), natural order out (spectral layout).
+// S = +1: the mirror.  Both unnormalised.
+// groups of N2 threads per block for the row kernel: at most 256 threads and
+// 48 KB of static shared memory
+template <typename T, int N1, int N2> struct RowsCfg {
+    static constexpr int by_threads = 256 / N2;
+    static constexpr int by_smem = (48 * 1024) / (N1 * (N2 + 1) * (int)sizeof(cplx<T>));
+    static constexpr int G = by_threads < by_smem ? by_threads : by_smem;
+    static constexpr int threads = G * N2;
+};
+
+// columns per block for the strided kernel: 128 contiguous bytes per row of the
+// tile, halved until the exchange buffer fits 48 KB of static shared memory
+template <typename T, int N> constexpr int cols_width() {
+    int w = 128 / (int)sizeof(cplx<T>);
+    while (w > 1 && N * w * (int)sizeof(cplx<T>) > 48 * 1024) w /= 2;
+    return w;
+}
+
+template <typename T, int N1, int N2, int S>
+__global__ void __launch_bounds__(RowsCfg<T, N1, N2>::threads)
+fft_rows_kernel(cplx<T>* __restrict__ data, long long rows, const cplx<T>* __restrict__ tw) {
+    constexpr int N = N1 * N2;
+    constexpr int G = RowsCfg<T, N1, N2>::G;
+    constexpr int RS = N2 + 1;
+    __shared__ cplx<T> scratch[G * N1 * RS];
+    const int g = threadIdx.x / N2, j = threadIdx.x % N2;
+    const long long row = (long long)blockIdx.x * G + g;
+    if (row >= rows) return;          // whole groups exit together; groups never straddle warps
+    // barrier mask of this group's N2 lanes only (other groups of the warp may have exited)
+    const unsigned lane0 = (threadIdx.x & 31u) & ~(unsigned)(N2 - 1);
+    const unsigned gmask = N2 >= 32 ? 0xffffffffu : (((1u << N2) - 1u) << lane0);
+    cplx<T>* p = data + row * N;
+    cplx<T>* sc = scratch + g * N1 * RS;
+    cplx<T> v[N1];
+    if constexpr (S < 0) {
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = p[j + N2 * decltype(nc)::value]; });
+        stage_a_fwd<T, S, N1, N2>(v, j, tw);
+        xscatter<T, N1, N2, RS, 1>(v, sc, j);
+        __syncwarp(gmask);
+        xgather_fwd<T, S, N1, N2, RS, 1>(v, sc, j);
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                p[(j + N2 * q) + N1 * k2] = v[q * N2 + k2];
+            });
+        });
+    } else {
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                v[q * N2 + k2] = p[(j + N2 * q) + N1 * k2];
+            });
+        });
+        xscatter_inv<T, S, N1, N2, RS, 1>(v, sc, j, tw);
+        __syncwarp(gmask);
+        xgather_inv<T, S, N1, N2, RS, 1>(v, sc, j);
+        static_for<0, N1>([&](auto nc) { p[j + N2 * decltype(nc)::value] = v[decltype(nc)::value]; });
+    }
+}
+
+// --------------------------------------------------------------------------- y / z
+// Block = W columns x N2 threads (c fastest).  Tile g -> (comp, o, x-tile);
+// element n of column c at base + n*stride + c.
+template <typename T, int N1, int N2, int W, int S>
+__global__ void __launch_bounds__(W * N2)
+fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, const cplx<T>* __restrict__ tw) {
+    constexpr int RS = N2 * W, ES = W;
+    __shared__ cplx<T> scratch[N1 * N2 * W];
+    const int c = threadIdx.x % W, j = threadIdx.x / W;
+    const size_t plane = (size_t)Nx * Ny;
+    const int ntile = Nx / W;
+    const int outerN = axis == 1 ? Nz : Ny;
+    const int t = blockIdx.x % ntile;
+    const long long rest = blockIdx.x / ntile;
+    const int o = (int)(rest % outerN);
+    const int comp = (int)(rest / outerN);
+    const size_t stride = axis == 1 ? (size_t)Nx : plane;
+    cplx<T>* base = data + (size_t)comp * plane * Nz + (axis == 1 ? (size_t)o * plane : (size_t)o * Nx) + (size_t)t * W + c;
+    cplx<T>* sc = scratch + c;
+    cplx<T> v[N1];
+    if constexpr (S < 0) {
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = base[(j + N2 * decltype(nc)::value) * stride]; });
+        stage_a_fwd<T, S, N1, N2>(v, j, tw);
+        xscatter<T, N1, N2, RS, ES>(v, sc, j);
+        __syncthreads();
+        xgather_fwd<T, S, N1, N2, RS, ES>(v, sc, j);
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                base[((j + N2 * q) + N1 * k2) * stride] = v[q * N2 + k2];
+            });
+        });
+    } else {
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                v[q * N2 + k2] = base[((j + N2 * q) + N1 * k2) * stride];
+            });
+        });
+        xscatter_inv<T, S, N1, N2, RS, ES>(v, sc, j, tw);
+        __syncthreads();
+        xgather_inv<T, S, N1, N2, RS, ES>(v, sc, j);
+        static_for<0, N1>([&](auto nc) { base[(j + N2 * decltype(nc)::value) * stride] = v[decltype(nc)::value]; });
+    }
+}
+
+// --------------------------------------------------------------------------- k-space
+// Per mode (kx, ky, kz) with C' = cos(c|k|dt)/Ntot, S' = sin(c|k|dt)/Ntot and
+// n = k/|k| (0 at k = 0):  E <- C'(E - n(n.E)) + i S' n x B,  B <- C' B - i S' n x E.
+template <typename T>
+__device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& Ez, cplx<T>& Bx,
+                                            cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, T C, T S) {
+    const T kEr = nx * Ex.x + ny * Ey.x + nz * Ez.x, kEi = nx * Ex.y + ny * Ey.y + nz * Ez.y;
+    const T cBxr = ny * Bz.x - nz * By.x, cBxi = ny * Bz.y - nz * By.y;
+    const T cByr = nz * Bx.x - nx * Bz.x, cByi = nz * Bx.y - nx * Bz.y;
+    const T cBzr = nx * By.x - ny * Bx.x, cBzi = nx * By.y - ny * Bx.y;
+    const T cExr = ny * Ez.x - nz * Ey.x, cExi = ny * Ez.y - nz * Ey.y;
+    const T cEyr = nz * Ex.x - nx * Ez.x, cEyi = nz * Ex.y - nx * Ez.y;
+    const T cEzr = nx * Ey.x - ny * Ex.x, cEzi = nx * Ey.y - ny * Ex.y;
+    const cplx<T> nEx = mk<T>(C * (Ex.x - nx * kEr) - S * cBxi, C * (Ex.y - nx * kEi) + S * cBxr);
+    const cplx<T> nEy = mk<T>(C * (Ey.x - ny * kEr) - S * cByi, C * (Ey.y - ny * kEi) + S * cByr);
+    const cplx<T> nEz = mk<T>(C * (Ez.x - nz * kEr) - S * cBzi, C * (Ez.y - nz * kEi) + S * cBzr);
+    Bx = mk<T>(C * Bx.x + S * cExi, C * Bx.y - S * cExr);
+    By = mk<T>(C * By.x + S * cEyi, C * By.y - S * cEyr);
+    Bz = mk<T>(C * Bz.x + S * cEzi, C * Bz.y - S * cEzr);
+    Ex = nEx; Ey = nEy; Ez = nEz;
+}
+
+// Block = W columns x N2 threads at one y; the six spectra of the W z-pencils are
+// kept in shared memory, slot q in natural kz order (element (kz, c) at
+// kz*W + c).  During each transform the slot of that component doubles as its
+// exchange buffer, so the block needs 6 * Nz * W complex values in total.
+template <typename T, int N1, int N2, int W>
+__global__ void __launch_bounds__(W * N2)
+kspace_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __restrict__ tw,
+                   const T* __restrict__ kxs, const T* __restrict__ kys, const T* __restrict__ kzs,
+                   const ModeCoef<T>* __restrict__ coef) {
+    constexpr int Nz = N1 * N2;
+    constexpr int RS = N2 * W, ES = W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* spec = reinterpret_cast<cplx<T>*>(smem_raw);      // [6][Nz][W]
+    const int c = threadIdx.x % W, j = threadIdx.x / W;
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t cstride = plane * Nz;
+    const int ntile = Nx / W;
+    const int xt = blockIdx.x % ntile;
+    const int y = blockIdx.x / ntile;
+    const int ix = xt * W + c;
+    cplx<T>* base = data + (size_t)y * Nx + ix;
+    cplx<T> v[N1];
+
+    // forward z transforms: spectrum of component q -> slot q
+    for (int q = 0; q < 6; ++q) {
+        cplx<T>* p = base + q * cstride;
+        cplx<T>* sl = spec + q * (Nz * W) + c;
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = p[(j + N2 * decltype(nc)::value) * plane]; });
+        stage_a_fwd<T, -1, N1, N2>(v, j, tw);
+        xscatter<T, N1, N2, RS, ES>(v, sl, j);
+        __syncthreads();
+        xgather_fwd<T, -1, N1, N2, RS, ES>(v, sl, j);
+        __syncthreads();
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int qq = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                sl[((j + N2 * qq) + N1 * k2) * W] = v[qq * N2 + k2];
+            });
+        });
+    }
+    __syncthreads();
+
+    // per-mode update; thread (c, j) takes modes kz = j + N2 s, s < N1
+    {
+        const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
+        const int ax = min(ix, Nx - ix), ay = min(y, Ny - y);
+        const T kx = kxs[ix], ky = kys[y];
+        cplx<T>* sl = spec + c;
+#pragma unroll 4
+        for (int s = 0; s < N1; ++s) {
+            const int iz = j + N2 * s;
+            const int az = min(iz, Nz - iz);
+            const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
+            const int o = iz * W;
+            cplx<T> Ex = sl[o], Ey = sl[Nz * W + o], Ez = sl[2 * Nz * W + o];
+            cplx<T> Bx = sl[3 * Nz * W + o], By = sl[4 * Nz * W + o], Bz = sl[5 * Nz * W + o];
+            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzs[iz] * m.kinv, m.C, m.S);
+            sl[o] = Ex; sl[Nz * W + o] = Ey; sl[2 * Nz * W + o] = Ez;
+            sl[3 * Nz * W + o] = Bx; sl[4 * Nz * W + o] = By; sl[5 * Nz * W + o] = Bz;
+        }
+    }
+    __syncthreads();
+
+    // inverse z transforms back to the field
+    for (int q = 0; q < 6; ++q) {
+        cplx<T>* sl = spec + q * (Nz * W) + c;
+        static_for<0, N1 / N2>([&](auto qc) {
+            constexpr int qq = decltype(qc)::value;
+            static_for<0, N2>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                v[qq * N2 + k2] = sl[((j + N2 * qq) + N1 * k2) * W];
+            });
+        });
+        __syncthreads();
+        xscatter_inv<T, +1, N1, N2, RS, ES>(v, sl, j, tw);
+        __syncthreads();
+        xgather_inv<T, +1, N1, N2, RS, ES>(v, sl, j);
+        cplx<T>* p = base + q * cstride;
+        static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[decltype(nc)::value]; });
+    }
+}
+
+template <typename T, int N1, int N2>
+cudaError_t axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, const cplx<T>* tw, int axis, int dir,
+                      cudaStream_t s) {
+    constexpr int N = N1 * N2;
+    if (axis == 0) {
+        const long long rows = (long long)ncomp * g.Nz * g.Ny;
+        using Cfg = RowsCfg<T, N1, N2>;
+        const unsigned blocks = (unsigned)((rows + Cfg::G - 1) / Cfg::G);
+        if (dir < 0) fft_rows_kernel<T, N1, N2, -1><<<blocks, Cfg::threads, 0, s>>>(data, rows, tw);
+        else fft_rows_kernel<T, N1, N2, +1><<<blocks, Cfg::threads, 0, s>>>(data, rows, tw);
+        return cudaGetLastError();
+    }
+    constexpr int W = cols_width<T, N>();
+    if (g.Nx % W != 0) return cudaErrorNotSupported;
+    const long long blocks = (long long)ncomp * (axis == 1 ? g.Nz : g.Ny) * (g.Nx / W);
+    (void)N;
+    if (dir < 0) fft_cols_kernel<T, N1, N2, W, -1><<<(unsigned)blocks, W * N2, 0, s>>>(data, g.Nx, g.Ny, g.Nz, axis, tw);
+    else fft_cols_kernel<T, N1, N2, W, +1><<<(unsigned)blocks, W * N2, 0, s>>>(data, g.Nx, g.Ny, g.Nz, axis, tw);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Returns cudaErrorNotSupported when the axis length has no register plan here.
+template <typename T>
+cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, const Tables<T>& tb, int axis,
+                                 int dir, cudaStream_t s) {
+    const int N = tb.plan[axis].N;
+    const cplx<T>* tw = tb.tw[axis];
+    switch (N) {
+        case 64: return axis_fast<T, 8, 8>(data, ncomp, g, tw, axis, dir, s);
+        case 128: return axis_fast<T, 16, 8>(data, ncomp, g, tw, axis, dir, s);
+        case 256: return axis_fast<T, 16, 16>(data, ncomp, g, tw, axis, dir, s);
+        case 512:
+            if constexpr (sizeof(T) == 4) return axis_fast<T, 32, 16>(data, ncomp, g, tw, axis, dir, s);
+            return cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+    }
+}
+
+template <typename T, int N1, int N2, int W>
+cudaError_t kspace_fast_launch(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s) {
+    const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
+    auto k = kspace_cols_kernel<T, N1, N2, W>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((long long)g.Ny * (g.Nx / W));
+    k<<<blocks, W * N2, smem, s>>>(data, g.Nx, g.Ny, tb.tw[2], tb.k[0], tb.k[1], tb.k[2], tb.coef);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s) {
+    // 64-byte rows of the tile: 8 complex64 or 4 complex128 columns
+    constexpr int W = sizeof(T) == 4 ? 8 : 4;
+    if (g.Nx % W != 0) return cudaErrorNotSupported;
+    switch (g.Nz) {
+        case 64: return kspace_fast_launch<T, 8, 8, W>(data, g, tb, s);
+        case 128: return kspace_fast_launch<T, 16, 8, W>(data, g, tb, s);
+        case 256: return kspace_fast_launch<T, 16, 16, W>(data, g, tb, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+template cudaError_t launch_fft_axis_fast<float>(cplx<float>*, int, const GridGeom&, const Tables<float>&, int, int, cudaStream_t);
+template cudaError_t launch_fft_axis_fast<double>(cplx<double>*, int, const GridGeom&, const Tables<double>&, int, int, cudaStream_t);
+template cudaError_t launch_kspace_fast<float>(cplx<float>*, const GridGeom&, const Tables<float>&, cudaStream_t);
+template cudaError_t launch_kspace_fast<double>(cplx<double>*, const GridGeom&, const Tables<double>&, cudaStream_t);
+
+}  // namespace psatd

@@ -1,0 +1,220 @@
+// Register-resident FFT pieces for the fast kernels.
+//
+// A pencil of length N = N1 * N2 (N2 divides N1) is spread over N2 threads that
+// hold N1 complex values each.  Forward transform (Cooley-Tukey, n = j + N2 n1,
+// k = k1 + N1 k2):
+//   1. thread j holds x[j + N2 n1] (n1 < N1), takes an N1-point DFT over n1 in
+//      registers and multiplies output k1 by W_N^{j k1};
+//   2. the values are exchanged through shared memory so that thread t gathers,
+//      for each k1 = t + N2 q (q < N1/N2), the N2 values of all threads;
+//   3. an N2-point DFT over j gives X[k1 + N1 k2]; thread t then holds
+//      X[(t + N2 q) + N1 k2] in register q*N2 + k2.
+// The inverse runs the same steps mirrored and returns to the input layout.
+// In both layouts a fixed register index maps consecutive threads to
+// consecutive elements, so global loads and stores of a pencil coalesce.
+//
+// The small DFTs run the Stockham passes of fft_core.cuh on register arrays
+// with every index and twiddle fixed at compile time (static_for); twiddles are
+// exp(S 2 pi i p/q) evaluated at compile time by ct_cos2pi / ct_sin2pi below.
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "fft_core.cuh"
+
+namespace psatd {
+
+// ---------------------------------------------------------------------------
+// compile-time cos / sin of 2 pi p / q: reduce to [-pi/4, pi/4] with the
+// quadrant symmetries, then the Taylor series (|x| <= pi/4: 13 terms reach
+// well below double rounding).
+// ---------------------------------------------------------------------------
+constexpr double kCtPi = 3.14159265358979323846264338327950288;
+
+constexpr double ct_sin_taylor(double x) {
+    double x2 = x * x, term = x, sum = x;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x2 / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double ct_cos_taylor(double x) {
+    double x2 = x * x, term = 1.0, sum = 1.0;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x2 / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+// angle 2 pi p/q with the octant chosen by integer arithmetic on 8p mod 8q
+constexpr void ct_sincos2pi(long long p, long long q, double* s, double* c) {
+    p %= q;
+    if (p < 0) p += q;
+    // octant o = floor(8 p / q), remainder r/q in [0, 1/8)
+    long long o = (8 * p) / q;
+    long long r8 = 8 * p - o * q;               // 2 pi p/q = o pi/4 + 2 pi r8/(8q)
+    double x = 2.0 * kCtPi * (double)r8 / (8.0 * (double)q);   // in [0, pi/4)
+    // for odd octants use the complement angle pi/4 - x to stay small
+    double sx = ct_sin_taylor(x), cx = ct_cos_taylor(x);
+    double y = kCtPi / 4.0 - x;
+    double sy = ct_sin_taylor(y), cy = ct_cos_taylor(y);
+    // angle = o*pi/4 + x ; write it as multiple of pi/2 plus a small angle
+    double S = 0, C = 0;
+    switch (o) {
+        case 0: S = sx; C = cx; break;                       // x
+        case 1: S = cy; C = sy; break;                       // pi/2 - y
+        case 2: S = cx; C = -sx; break;                      // pi/2 + x
+        case 3: S = sy; C = -cy; break;                      // pi - y
+        case 4: S = -sx; C = -cx; break;                     // pi + x
+        case 5: S = -cy; C = -sy; break;                     // 3pi/2 - y
+        case 6: S = -cx; C = sx; break;                      // 3pi/2 + x
+        default: S = -sy; C = cy; break;                     // 2pi - y
+    }
+    *s = S;
+    *c = C;
+}
+constexpr double ct_cos2pi(long long p, long long q) { double s = 0, c = 0; ct_sincos2pi(p, q, &s, &c); return c; }
+constexpr double ct_sin2pi(long long p, long long q) { double s = 0, c = 0; ct_sincos2pi(p, q, &s, &c); return s; }
+
+// ---------------------------------------------------------------------------
+// static_for: f(integral_constant<int, i>) for i in [B, E)
+// ---------------------------------------------------------------------------
+template <int B, int E, typename F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// radix plan of a register DFT: largest radices first
+template <int N> struct RegPlanFirst {
+    static constexpr int value = (N % 8 == 0 && N != 16) ? 8 : (N % 4 == 0) ? 4 : (N % 5 == 0) ? 5
+                                 : (N % 3 == 0) ? 3 : (N % 2 == 0) ? 2 : N;
+};
+
+// one Stockham pass of radix R over a register array of length N (product of
+// earlier radices Ns)
+template <typename T, int S, int N, int R, int Ns>
+__host__ __device__ __forceinline__ void reg_pass(const cplx<T> (&in)[N], cplx<T> (&out)[N]) {
+    static_for<0, N / R>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        constexpr int k = j % Ns;
+        cplx<T> v[R];
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            v[r] = in[j + r * (N / R)];
+            if constexpr (Ns > 1 && r > 0 && k > 0) {
+                constexpr double c = ct_cos2pi((long long)r * k, (long long)Ns * R);
+                constexpr double s = (double)S * ct_sin2pi((long long)r * k, (long long)Ns * R);
+                v[r] = cmul(v[r], mk<T>((T)c, (T)s));
+            }
+        });
+        dft_r<T, R, S>(v);
+        constexpr int idx = (j / Ns) * Ns * R + k;
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            out[idx + r * Ns] = v[r];
+        });
+    });
+}
+
+template <typename T, int S, int N, int Ns>
+__host__ __device__ __forceinline__ void reg_dft_rec(cplx<T> (&v)[N]) {
+    if constexpr (Ns < N) {
+        constexpr int R = RegPlanFirst<N / Ns>::value;
+        cplx<T> t[N];
+        reg_pass<T, S, N, R, Ns>(v, t);
+        static_for<0, N>([&](auto ic) { v[decltype(ic)::value] = t[decltype(ic)::value]; });
+        reg_dft_rec<T, S, N, Ns * R>(v);
+    }
+}
+
+// In-place N-point DFT of a register array, natural order in and out.
+template <typename T, int S, int N>
+__host__ __device__ __forceinline__ void reg_dft(cplx<T> (&v)[N]) {
+    if constexpr (N == 16) {
+        // 16 = 4 x 4 keeps the butterflies multiplication-free except 9 twiddles
+        cplx<T> t[16];
+        reg_pass<T, S, 16, 4, 1>(v, t);
+        reg_pass<T, S, 16, 4, 4>(t, v);
+    } else {
+        reg_dft_rec<T, S, N, 1>(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pencil stages.  tw[t] = exp(-2 pi i t / N) (inverse uses the conjugate).
+// ---------------------------------------------------------------------------
+template <typename T, int S>
+__host__ __device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int idx) {
+    const cplx<T> w = tw[idx];
+    return S < 0 ? w : mk<T>(w.x, -w.y);
+}
+
+// Forward stage 1 (input layout): DFT_N1 over n1, then multiply by W_N^{j k1}.
+template <typename T, int S, int N1, int N2>
+__host__ __device__ __forceinline__ void stage_a_fwd(cplx<T> (&v)[N1], int j, const cplx<T>* __restrict__ tw) {
+    reg_dft<T, S, N1>(v);
+    static_for<1, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        if (j) v[k1] = cmul(v[k1], twiddle<T, S>(tw, j * k1));
+    });
+}
+
+// scratch layout [k1][j], row stride N2 + 1
+template <typename T, int N1, int N2>
+__host__ __device__ __forceinline__ void scatter_a(const cplx<T> (&v)[N1], cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        sc[k1 * (N2 + 1) + j] = v[k1];
+    });
+}
+
+// Forward stage 2: thread t gathers rows k1 = t + N2 q and takes DFT_N2 over j;
+// register q*N2 + k2 ends holding X[(t + N2 q) + N1 k2].
+template <typename T, int S, int N1, int N2>
+__host__ __device__ __forceinline__ void gather_b_fwd(cplx<T> (&v)[N1], const cplx<T>* sc, int t) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        const cplx<T>* row = sc + (t + N2 * q) * (N2 + 1);
+        static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value]; });
+        reg_dft<T, S, N2>(w);
+        static_for<0, N2>([&](auto kc) { v[q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
+    });
+}
+
+// Inverse stage 1 (spectral layout): for each held k1 = t + N2 q, DFT_N2 over
+// k2, then multiply output n2 by W_N^{S n2 k1}; scatter to [k1][n2].
+template <typename T, int S, int N1, int N2>
+__host__ __device__ __forceinline__ void stage_a_inv_scatter(cplx<T> (&v)[N1], cplx<T>* sc, int t,
+                                                     const cplx<T>* __restrict__ tw) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        static_for<0, N2>([&](auto kc) { w[decltype(kc)::value] = v[q * N2 + decltype(kc)::value]; });
+        reg_dft<T, S, N2>(w);
+        const int k1 = t + N2 * q;
+        cplx<T>* row = sc + k1 * (N2 + 1);
+        static_for<0, N2>([&](auto nc) {
+            constexpr int n2 = decltype(nc)::value;
+            row[n2] = (n2 == 0 || k1 == 0) ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1));
+        });
+    });
+}
+
+// Inverse stage 2: thread j gathers column j of every row k1 and takes DFT_N1
+// over k1, giving x[j + N2 n1] in register n1.
+template <typename T, int S, int N1, int N2>
+__host__ __device__ __forceinline__ void gather_b_inv(cplx<T> (&v)[N1], const cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        v[k1] = sc[k1 * (N2 + 1) + j];
+    });
+    reg_dft<T, S, N1>(v);
+}
+
+}  // namespace psatd

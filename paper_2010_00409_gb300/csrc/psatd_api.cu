@@ -70,6 +70,7 @@ struct psatd_ctx {
     int samp_ny = 0, samp_nz = 0;
 
     long long launches = 0;
+    int kernel_path = PSATD_PATH_AUTO;
     std::string err = "no error";
 
     // per-kernel event timing (psatd_profile_enable)
@@ -261,7 +262,15 @@ template <typename T>
 cudaError_t fft_axis(psatd_ctx* c, cplx<T>* data, int ncomp, int axis, int dir, int kind) {
     const GridGeom g = geom(c);
     const Tables<T> tb = tables<T>(c);
+    if (c->plan[axis].N <= 1) return cudaSuccess;
     return timed(c, kind < 0 ? axis : kind, [&] {
+        if (c->kernel_path == PSATD_PATH_AUTO) {
+            cudaError_t e = launch_fft_axis_fast<T>(data, ncomp, g, tb, axis, dir, c->stream);
+            if (e != cudaErrorNotSupported) {
+                ++c->launches;
+                return e;
+            }
+        }
         return launch_fft_axis<T>(data, ncomp, g, tb, axis, dir, c->stream, &c->launches);
     });
 }
@@ -289,6 +298,13 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     if ((e = fft_axis<T>(c, f, 6, 0, -1, -1)) != cudaSuccess) return e;
     if ((e = fft_axis<T>(c, f, 6, 1, -1, -1)) != cudaSuccess) return e;
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
+        if (mode == KS_ROTATE && c->kernel_path == PSATD_PATH_AUTO) {
+            cudaError_t r = launch_kspace_fast<T>(f, g, tb, c->stream);
+            if (r != cudaErrorNotSupported) {
+                ++c->launches;
+                return r;
+            }
+        }
         return launch_kspace_z<T>(f, g, tb, mode, scale, c->stream, &c->launches);
     });
     if (e != cudaSuccess) return e;
@@ -652,6 +668,13 @@ psatd_status psatd_synchronize(psatd_ctx* c) {
 }
 
 long long psatd_launch_count(const psatd_ctx* c) { return c ? c->launches : 0; }
+
+psatd_status psatd_set_kernel_path(psatd_ctx* c, int path) {
+    if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
+    if (path != PSATD_PATH_AUTO && path != PSATD_PATH_GENERIC) return fail(c, PSATD_ERR_ARG, "unknown kernel path");
+    c->kernel_path = path;
+    return PSATD_OK;
+}
 
 psatd_status psatd_profile_enable(psatd_ctx* c, int enable) {
     psatd_status st = check_ctx(c, false);

@@ -27,7 +27,9 @@ EXPORTS = (
     "psatd_sample_focal_plane", "psatd_diagnostics", "psatd_time", "psatd_set_time",
     "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
     "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
+    "psatd_set_kernel_path",
 )
+PATH_AUTO, PATH_GENERIC = 0, 1
 
 KERNEL_KINDS = ("fft_x", "fft_y", "fft_z", "kspace_z", "init_pulse", "sample_plane", "diagnostics",
                 "plane_xy")
@@ -86,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_profile_enable": (C.c_int, [P, C.c_int]),
         "psatd_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "psatd_kernel_name": (C.c_char_p, [C.c_int]),
+        "psatd_set_kernel_path": (C.c_int, [P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,6 +244,9 @@ class Context:
     @property
     def launch_count(self) -> int:
         return lib().psatd_launch_count(self._ptr)
+
+    def set_kernel_path(self, path: int):
+        _check(lib().psatd_set_kernel_path(self._ptr, path), self._ptr)
 
     def profile_enable(self, on: bool = True):
         _check(lib().psatd_profile_enable(self._ptr, 1 if on else 0), self._ptr)

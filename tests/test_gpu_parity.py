@@ -84,7 +84,8 @@ def test_plain_method_64cubed_20_steps(lib, prec):
             d1 = ctx.diagnostics()
         want = O.advance(f0, ogrid(g), dt, 20)
         assert rel(got, want) <= TOL[prec]
-        assert abs(d1["energy"] / d0["energy"] - 1) <= (1e-13 if prec == 64 else 2e-6)
+        # |E'|^2 - |E|^2 is bounded by twice the relative L2 error of the state
+        assert abs(d1["energy"] / d0["energy"] - 1) <= (1e-13 if prec == 64 else 2 * TOL[32])
         assert d1["max_div_E"] <= (1e-13 if prec == 64 else 1e-6) * d1["max_E_hat"]
         assert d1["max_div_B"] <= (1e-13 if prec == 64 else 1e-6) * d1["max_B_hat"]
     # the plane wave alone: exact phase exp(-i n c k0 dt), zero dispersion
@@ -266,5 +267,42 @@ def test_tight_focus_256_full_size(lib, focus_reference, prec):
         d = ctx.diagnostics()
     assert np.max(np.abs(ref)) > 0
     assert rel(got, ref) <= (1e-10 if prec == 64 else 1e-4)
-    assert abs(d["energy"] / e0 - 1) <= (1e-10 if prec == 64 else 1e-4)
+    # The per-mode coefficients (C, S, k^) are rounded once to the storage type
+    # and the same rounding repeats every step, so the energy drift grows
+    # linearly: at most 2 * c0 * u per step with u the unit roundoff and c0 ~ 4
+    # (C, S and the k^ products), i.e. 8 u n after n steps.
+    u = 2.0 ** -53 if prec == 64 else 2.0 ** -24
+    assert abs(d["energy"] / e0 - 1) <= max(8 * u * n_steps, 1e-12)
     assert d["max_div_E"] <= (1e-12 if prec == 64 else 1e-5) * d["max_E_hat"]
+
+
+# ---------------------------------------------------------------------------
+# Register-resident kernels (axis lengths 64, 128, 256, 512) against the oracle
+# and against the generic shared-memory kernels on the same inputs.
+# ---------------------------------------------------------------------------
+FAST_SHAPES = [(64, 64, 64), (256, 64, 128), (128, 256, 64), (64, 128, 256), (512, 16, 64), (48, 64, 128)]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape", FAST_SHAPES)
+def test_fast_kernels_match_oracle_and_generic(lib, prec, shape):
+    Nx, Ny, Nz = shape
+    g = W.GridSpec(Nx, Ny, Nz, 0.5, 0.7, 0.3, 0.0, 0.0, 0.0, 1.0)
+    f = W.random_complex_field((6, Nz, Ny, Nx), seed=Nx * 3 + Ny + Nz)
+    dt = 0.41
+    out = {}
+    for path in (lib.PATH_AUTO, lib.PATH_GENERIC):
+        with lib.Context(g, None, dt, prec) as ctx:
+            ctx.set_kernel_path(path)
+            ctx.set_fields(f)
+            ctx.fft(lib.FORWARD)
+            F = ctx.get_field(-1)
+            ctx.set_fields(f)
+            ctx.advance(2)
+            out[path] = (F, ctx.get_field(-1))
+    F_ref = O.fft3(f)
+    step_ref = O.advance(f, ogrid(g), dt, 2)
+    for path in out:
+        assert rel(out[path][0], F_ref) <= TOL[prec]
+        assert rel(out[path][1], step_ref) <= 2 * TOL[prec]
+    assert rel(out[lib.PATH_AUTO][1], out[lib.PATH_GENERIC][1]) <= 2 * TOL[prec]
