@@ -167,7 +167,10 @@ psatd_status psatd_diagnostics(psatd_ctx* ctx, psatd_diag* out);
 double psatd_time(const psatd_ctx* ctx);
 psatd_status psatd_set_time(psatd_ctx* ctx, double t);
 
-/* Wait for all work of the context's stream. */
+/* Wait for all work of the context's stream.  Returns PSATD_ERR_TIMEOUT if a
+ * kernel reported an expired bounded wait since the last check (the affected
+ * step left the field unchanged); the error word is then cleared.  get_field
+ * to host, sample_focal_plane to host and diagnostics check it too. */
 psatd_status psatd_synchronize(psatd_ctx* ctx);
 
 /* Eq. 12: D_min = -R_min cos(theta) + sqrt(R_max^2 - R_min^2 sin^2(theta)). */
@@ -184,11 +187,18 @@ const char* psatd_status_string(psatd_status s);
 long long psatd_launch_count(const psatd_ctx* ctx);
 
 /* Kernel selection: AUTO uses the register-resident kernels where the axis
- * length has one (64, 128, 256, 512) and the generic shared-memory Stockham
- * kernels elsewhere; GENERIC forces the latter everywhere.  Both compute the
- * same transform; the default is AUTO. */
-enum { PSATD_PATH_AUTO = 0, PSATD_PATH_GENERIC = 1 };
+ * length has one (64, 128, 256, 512; the k-space pass for Nz in 64, 128, 256,
+ * fed by tensor copies), and the generic shared-memory Stockham kernels
+ * elsewhere; REGISTER is AUTO without the tensor-copy feed; GENERIC forces the
+ * generic kernels everywhere.  All compute the same transform; default AUTO. */
+enum { PSATD_PATH_AUTO = 0, PSATD_PATH_GENERIC = 1, PSATD_PATH_REGISTER = 2 };
 psatd_status psatd_set_kernel_path(psatd_ctx* ctx, int path);
+
+/* Self-test of device wait reporting: launches one block that waits, with a
+ * short bound, on a barrier nothing completes, and returns what
+ * psatd_synchronize reports (PSATD_ERR_TIMEOUT when the bound works).  The
+ * context stays usable afterwards.  The paper has no counterpart. */
+psatd_status psatd_selftest_wait_timeout(psatd_ctx* ctx);
 
 /* Kernel kinds for per-kernel timing. */
 enum {

@@ -2,6 +2,7 @@
 // per-axis FFT plan, and the launch interfaces of the kernel translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,6 +97,22 @@ cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, co
                                  int axis, int dir, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
+
+// Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
+// 8-byte elements {Nx * sizeof(complex)/8, Ny, Nz, 6} with box
+// {kspace_tma_box_x(prec), 1, Nz, 1}.  Device errors are OR-ed into *err.
+template <typename T>
+cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
+                              int* err, cudaStream_t s);
+int kspace_tma_box_x(int prec);
+cudaError_t launch_wait_timeout_selftest(int* err, cudaStream_t s);
+
+// Fused x+y FFT of x-y planes through a thread-block cluster (distributed
+// shared memory); cudaErrorNotSupported (nothing launched) for other shapes.
+template <typename T>
+cudaError_t launch_plane_xy(cplx<T>* data, int ncomp, const GridGeom& g, const Tables<T>& tb, int dir,
+                            cudaStream_t s);
+bool plane_xy_supported(int prec, const GridGeom& g);
 
 // Fused z-forward FFT, per-mode update, z-inverse FFT over all six components.
 template <typename T>

@@ -15,53 +15,6 @@ namespace psatd {
 
 namespace {
 
-// exchange helpers with an explicit layout: element (k1, j) at k1*RS + j*ES
-template <typename T, int N1, int N2, int RS, int ES>
-__device__ __forceinline__ void xscatter(const cplx<T> (&v)[N1], cplx<T>* sc, int j) {
-    static_for<0, N1>([&](auto kc) {
-        constexpr int k1 = decltype(kc)::value;
-        sc[k1 * RS + j * ES] = v[k1];
-    });
-}
-
-template <typename T, int S, int N1, int N2, int RS, int ES>
-__device__ __forceinline__ void xgather_fwd(cplx<T> (&v)[N1], const cplx<T>* sc, int t) {
-    static_for<0, N1 / N2>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        cplx<T> w[N2];
-        const cplx<T>* row = sc + (t + N2 * q) * RS;
-        static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value * ES]; });
-        reg_dft<T, S, N2>(w);
-        static_for<0, N2>([&](auto kc) { v[q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
-    });
-}
-
-template <typename T, int S, int N1, int N2, int RS, int ES>
-__device__ __forceinline__ void xscatter_inv(cplx<T> (&v)[N1], cplx<T>* sc, int t,
-                                             const cplx<T>* __restrict__ tw) {
-    static_for<0, N1 / N2>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        cplx<T> w[N2];
-        static_for<0, N2>([&](auto kc) { w[decltype(kc)::value] = v[q * N2 + decltype(kc)::value]; });
-        reg_dft<T, S, N2>(w);
-        const int k1 = t + N2 * q;
-        cplx<T>* row = sc + k1 * RS;
-        static_for<0, N2>([&](auto nc) {
-            constexpr int n2 = decltype(nc)::value;
-            row[n2 * ES] = (n2 == 0) ? w[n2] : (k1 == 0 ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1)));
-        });
-    });
-}
-
-template <typename T, int S, int N1, int N2, int RS, int ES>
-__device__ __forceinline__ void xgather_inv(cplx<T> (&v)[N1], const cplx<T>* sc, int j) {
-    static_for<0, N1>([&](auto kc) {
-        constexpr int k1 = decltype(kc)::value;
-        v[k1] = sc[k1 * RS + j * ES];
-    });
-    reg_dft<T, S, N1>(v);
-}
-
 // --------------------------------------------------------------------------- x
 // S = -1: natural order in (input layout), natural order out (spectral layout).
 // S = +1: the mirror.  Both unnormalised.
@@ -175,27 +128,6 @@ fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, co
 }
 
 // --------------------------------------------------------------------------- k-space
-// Per mode (kx, ky, kz) with C' = cos(c|k|dt)/Ntot, S' = sin(c|k|dt)/Ntot and
-// n = k/|k| (0 at k = 0):  E <- C'(E - n(n.E)) + i S' n x B,  B <- C' B - i S' n x E.
-template <typename T>
-__device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& Ez, cplx<T>& Bx,
-                                            cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, T C, T S) {
-    const T kEr = nx * Ex.x + ny * Ey.x + nz * Ez.x, kEi = nx * Ex.y + ny * Ey.y + nz * Ez.y;
-    const T cBxr = ny * Bz.x - nz * By.x, cBxi = ny * Bz.y - nz * By.y;
-    const T cByr = nz * Bx.x - nx * Bz.x, cByi = nz * Bx.y - nx * Bz.y;
-    const T cBzr = nx * By.x - ny * Bx.x, cBzi = nx * By.y - ny * Bx.y;
-    const T cExr = ny * Ez.x - nz * Ey.x, cExi = ny * Ez.y - nz * Ey.y;
-    const T cEyr = nz * Ex.x - nx * Ez.x, cEyi = nz * Ex.y - nx * Ez.y;
-    const T cEzr = nx * Ey.x - ny * Ex.x, cEzi = nx * Ey.y - ny * Ex.y;
-    const cplx<T> nEx = mk<T>(C * (Ex.x - nx * kEr) - S * cBxi, C * (Ex.y - nx * kEi) + S * cBxr);
-    const cplx<T> nEy = mk<T>(C * (Ey.x - ny * kEr) - S * cByi, C * (Ey.y - ny * kEi) + S * cByr);
-    const cplx<T> nEz = mk<T>(C * (Ez.x - nz * kEr) - S * cBzi, C * (Ez.y - nz * kEi) + S * cBzr);
-    Bx = mk<T>(C * Bx.x + S * cExi, C * Bx.y - S * cExr);
-    By = mk<T>(C * By.x + S * cEyi, C * By.y - S * cEyr);
-    Bz = mk<T>(C * Bz.x + S * cEzi, C * Bz.y - S * cEzr);
-    Ex = nEx; Ey = nEy; Ez = nEz;
-}
-
 // Block = W columns x N2 threads at one y; the six spectra of the W z-pencils are
 // kept in shared memory, slot q in natural kz order (element (kz, c) at
 // kz*W + c).  During each transform the slot of that component doubles as its

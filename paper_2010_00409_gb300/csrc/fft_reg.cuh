@@ -217,4 +217,98 @@ __host__ __device__ __forceinline__ void gather_b_inv(cplx<T> (&v)[N1], const cp
     reg_dft<T, S, N1>(v);
 }
 
+// ---------------------------------------------------------------------------
+// 16 x 16 transpose across the 16 lanes of a group by four XOR-shuffle stages:
+// on entry lane j holds a_j[i] in v[i]; on exit lane t holds a_n[t] in v[n].
+// Register indices are compile-time; the lane bit only selects values.
+template <typename T>
+__device__ __forceinline__ void lane_transpose16(cplx<T> (&v)[16], int lane) {
+    static_for<0, 4>([&](auto sc) {
+        constexpr int sbit = 8 >> decltype(sc)::value;
+        const bool up = (lane & sbit) != 0;
+        static_for<0, 16>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            if constexpr ((i & sbit) == 0) {
+                constexpr int ip = i | sbit;
+                const cplx<T> send = up ? v[i] : v[ip];
+                cplx<T> recv;
+                recv.x = __shfl_xor_sync(0xffffffffu, send.x, sbit, 16);
+                recv.y = __shfl_xor_sync(0xffffffffu, send.y, sbit, 16);
+                if (up) v[i] = recv;
+                else v[ip] = recv;
+            }
+        });
+    });
+}
+
+// ---------------------------------------------------------------------------
+// exchange helpers with an explicit layout: element (k1, j) at k1*RS + j*ES
+template <typename T, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xscatter(const cplx<T> (&v)[N1], cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        sc[k1 * RS + j * ES] = v[k1];
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xgather_fwd(cplx<T> (&v)[N1], const cplx<T>* sc, int t) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        const cplx<T>* row = sc + (t + N2 * q) * RS;
+        static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value * ES]; });
+        reg_dft<T, S, N2>(w);
+        static_for<0, N2>([&](auto kc) { v[q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xscatter_inv(cplx<T> (&v)[N1], cplx<T>* sc, int t,
+                                             const cplx<T>* __restrict__ tw) {
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cplx<T> w[N2];
+        static_for<0, N2>([&](auto kc) { w[decltype(kc)::value] = v[q * N2 + decltype(kc)::value]; });
+        reg_dft<T, S, N2>(w);
+        const int k1 = t + N2 * q;
+        cplx<T>* row = sc + k1 * RS;
+        static_for<0, N2>([&](auto nc) {
+            constexpr int n2 = decltype(nc)::value;
+            row[n2 * ES] = (n2 == 0) ? w[n2] : (k1 == 0 ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1)));
+        });
+    });
+}
+
+template <typename T, int S, int N1, int N2, int RS, int ES>
+__device__ __forceinline__ void xgather_inv(cplx<T> (&v)[N1], const cplx<T>* sc, int j) {
+    static_for<0, N1>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        v[k1] = sc[k1 * RS + j * ES];
+    });
+    reg_dft<T, S, N1>(v);
+}
+
+// ---------------------------------------------------------------------------
+// Per mode (kx, ky, kz) with C' = cos(c|k|dt)/Ntot, S' = sin(c|k|dt)/Ntot and
+// n = k/|k| (0 at k = 0):  E <- C'(E - n(n.E)) + i S' n x B,  B <- C' B - i S' n x E.
+template <typename T>
+__device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& Ez, cplx<T>& Bx,
+                                            cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, T C, T S) {
+    const T kEr = nx * Ex.x + ny * Ey.x + nz * Ez.x, kEi = nx * Ex.y + ny * Ey.y + nz * Ez.y;
+    const T cBxr = ny * Bz.x - nz * By.x, cBxi = ny * Bz.y - nz * By.y;
+    const T cByr = nz * Bx.x - nx * Bz.x, cByi = nz * Bx.y - nx * Bz.y;
+    const T cBzr = nx * By.x - ny * Bx.x, cBzi = nx * By.y - ny * Bx.y;
+    const T cExr = ny * Ez.x - nz * Ey.x, cExi = ny * Ez.y - nz * Ey.y;
+    const T cEyr = nz * Ex.x - nx * Ez.x, cEyi = nz * Ex.y - nx * Ez.y;
+    const T cEzr = nx * Ey.x - ny * Ex.x, cEzi = nx * Ey.y - ny * Ex.y;
+    const cplx<T> nEx = mk<T>(C * (Ex.x - nx * kEr) - S * cBxi, C * (Ex.y - nx * kEi) + S * cBxr);
+    const cplx<T> nEy = mk<T>(C * (Ey.x - ny * kEr) - S * cByi, C * (Ey.y - ny * kEi) + S * cByr);
+    const cplx<T> nEz = mk<T>(C * (Ez.x - nz * kEr) - S * cBzi, C * (Ez.y - nz * kEi) + S * cBzr);
+    Bx = mk<T>(C * Bx.x + S * cExi, C * Bx.y - S * cExr);
+    By = mk<T>(C * By.x + S * cEyi, C * By.y - S * cEyr);
+    Bz = mk<T>(C * Bz.x + S * cEzi, C * Bz.y - S * cEzr);
+    Ex = nEx; Ey = nEy; Ez = nEz;
+}
+
 }  // namespace psatd

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/psatd.h"
 #include "common.cuh"
 
@@ -71,6 +73,12 @@ struct psatd_ctx {
 
     long long launches = 0;
     int kernel_path = PSATD_PATH_AUTO;
+
+    // tensor map of the field storage for the copy-engine-fed k-space kernel
+    alignas(64) CUtensorMap field_map;
+    void* field_map_ptr = nullptr;      // storage the map was encoded for
+    bool field_map_ok = false;
+    int* dev_err = nullptr;             // device error word (bits of psatd::DeviceError)
     std::string err = "no error";
 
     // per-kernel event timing (psatd_profile_enable)
@@ -258,13 +266,67 @@ cudaError_t timed(psatd_ctx* c, int kind, F&& launch) {
     return cudaSuccess;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// (Re)encode the field tensor map when the storage changed; false if the
+// copy-engine path does not apply to this grid.
+bool ensure_field_map(psatd_ctx* c) {
+    if (c->field_map_ptr == c->fields) return c->field_map_ok;
+    c->field_map_ptr = c->fields;
+    c->field_map_ok = false;
+    const psatd_grid& g = c->grid;
+    if (g.Nz > 256 || !c->dev_err) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t es = cplx_size(c->prec), xw = es / 8;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.Nx * xw, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, 6};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.Nx * es, (cuuint64_t)g.Nx * g.Ny * es,
+                                   (cuuint64_t)g.Nx * g.Ny * g.Nz * es};
+    const cuuint32_t box[4] = {(cuuint32_t)kspace_tma_box_x(c->prec), 1, (cuuint32_t)g.Nz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (dims[0] < box[0] || (g.Nx * es) % 16 != 0) return false;
+    CUresult r = enc(&c->field_map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, c->fields, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->field_map_ok = (r == CUDA_SUCCESS);
+    return c->field_map_ok;
+}
+
+// Read and clear the device error word (synchronises the stream).
+psatd_status check_device_error(psatd_ctx* c) {
+    if (!c->dev_err) return PSATD_OK;
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h) {
+        CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return fail(c, PSATD_ERR_TIMEOUT, "a bounded device wait for a tensor copy expired; results of that step are invalid");
+    }
+    return PSATD_OK;
+}
+
 template <typename T>
 cudaError_t fft_axis(psatd_ctx* c, cplx<T>* data, int ncomp, int axis, int dir, int kind) {
     const GridGeom g = geom(c);
     const Tables<T> tb = tables<T>(c);
     if (c->plan[axis].N <= 1) return cudaSuccess;
     return timed(c, kind < 0 ? axis : kind, [&] {
-        if (c->kernel_path == PSATD_PATH_AUTO) {
+        if (c->kernel_path != PSATD_PATH_GENERIC) {
             cudaError_t e = launch_fft_axis_fast<T>(data, ncomp, g, tb, axis, dir, c->stream);
             if (e != cudaErrorNotSupported) {
                 ++c->launches;
@@ -275,9 +337,35 @@ cudaError_t fft_axis(psatd_ctx* c, cplx<T>* data, int ncomp, int axis, int dir, 
     });
 }
 
+// Fused x+y plane transform when the cluster kernel covers this plane shape
+// (AUTO path); returns cudaErrorNotSupported otherwise.
+template <typename T>
+cudaError_t plane_xy(psatd_ctx* c, cplx<T>* data, int ncomp, int dir, int kind) {
+    const GridGeom g = geom(c);
+    if (c->kernel_path != PSATD_PATH_AUTO || !plane_xy_supported(c->prec, g)) return cudaErrorNotSupported;
+    const Tables<T> tb = tables<T>(c);
+    return timed(c, kind < 0 ? (int)PSATD_KERNEL_PLANE_XY : kind, [&] {
+        ++c->launches;
+        return launch_plane_xy<T>(data, ncomp, g, tb, dir, c->stream);
+    });
+}
+
 template <typename T>
 cudaError_t fft3d(psatd_ctx* c, cplx<T>* data, int ncomp, int dir, int kind = -1) {
     cudaError_t e;
+    if (dir < 0) {
+        e = plane_xy<T>(c, data, ncomp, dir, kind);
+        if (e == cudaSuccess) return fft_axis<T>(c, data, ncomp, 2, dir, kind);
+        if (e != cudaErrorNotSupported) return e;
+    } else {
+        e = fft_axis<T>(c, data, ncomp, 2, dir, kind);
+        if (e != cudaSuccess) return e;
+        e = plane_xy<T>(c, data, ncomp, dir, kind);
+        if (e != cudaErrorNotSupported) return e;
+        e = fft_axis<T>(c, data, ncomp, 1, dir, kind);
+        if (e != cudaSuccess) return e;
+        return fft_axis<T>(c, data, ncomp, 0, dir, kind);
+    }
     const int order_f[3] = {0, 1, 2}, order_i[3] = {2, 1, 0};
     const int* order = dir < 0 ? order_f : order_i;
     for (int q = 0; q < 3; ++q) {
@@ -294,11 +382,22 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     const GridGeom g = geom(c);
     const Tables<T> tb = tables<T>(c);
     cplx<T>* f = static_cast<cplx<T>*>(c->fields);
-    cudaError_t e;
-    if ((e = fft_axis<T>(c, f, 6, 0, -1, -1)) != cudaSuccess) return e;
-    if ((e = fft_axis<T>(c, f, 6, 1, -1, -1)) != cudaSuccess) return e;
+    cudaError_t e = plane_xy<T>(c, f, 6, -1, -1);
+    const bool fused_xy = (e == cudaSuccess);
+    if (!fused_xy) {
+        if (e != cudaErrorNotSupported) return e;
+        if ((e = fft_axis<T>(c, f, 6, 0, -1, -1)) != cudaSuccess) return e;
+        if ((e = fft_axis<T>(c, f, 6, 1, -1, -1)) != cudaSuccess) return e;
+    }
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
-        if (mode == KS_ROTATE && c->kernel_path == PSATD_PATH_AUTO) {
+        if (mode == KS_ROTATE && c->kernel_path == PSATD_PATH_AUTO && ensure_field_map(c)) {
+            cudaError_t r = launch_kspace_tma<T>(c->field_map, f, g, tb, c->dev_err, c->stream);
+            if (r != cudaErrorNotSupported) {
+                ++c->launches;
+                return r;
+            }
+        }
+        if (mode == KS_ROTATE && c->kernel_path != PSATD_PATH_GENERIC) {
             cudaError_t r = launch_kspace_fast<T>(f, g, tb, c->stream);
             if (r != cudaErrorNotSupported) {
                 ++c->launches;
@@ -308,6 +407,7 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
         return launch_kspace_z<T>(f, g, tb, mode, scale, c->stream, &c->launches);
     });
     if (e != cudaSuccess) return e;
+    if (fused_xy) return plane_xy<T>(c, f, 6, +1, -1);
     if ((e = fft_axis<T>(c, f, 6, 1, +1, -1)) != cudaSuccess) return e;
     if ((e = fft_axis<T>(c, f, 6, 0, +1, -1)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -383,6 +483,11 @@ psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mappin
     if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGetDevice");
     if (st == PSATD_OK) st = precision == 64 ? upload_axis_tables<double>(c) : upload_axis_tables<float>(c);
     if (st == PSATD_OK) st = set_coef(c, dt);
+    if (st == PSATD_OK) {
+        e = cudaMalloc(&c->dev_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
+        if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(error word)");
+    }
     if (st == PSATD_OK && !(flags & PSATD_FLAG_NO_FIELD_ALLOC)) {
         const size_t bytes = 6 * n_cells(*grid) * cplx_size(precision);
         e = cudaMalloc(&c->fields, bytes);
@@ -412,6 +517,7 @@ void psatd_destroy(psatd_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     if (c->own_fields && c->fields) cudaFree(c->fields);
+    if (c->dev_err) cudaFree(c->dev_err);
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
@@ -474,6 +580,7 @@ static psatd_status copy_field(psatd_ctx* c, int comp, void* dst, const void* sr
     else kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(c, cudaMemcpyAsync(to_lib ? lib : dst, to_lib ? src : lib, bytes, kind, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    if (!to_lib && !on_device) return check_device_error(c);
     return PSATD_OK;
 }
 
@@ -599,6 +706,7 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
     if (!dst_on_device) {
         CK(c, cudaMemcpyAsync(dst, out, out_bytes, cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
+        return check_device_error(c);
     }
     return PSATD_OK;
 }
@@ -648,7 +756,7 @@ psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
     out->max_E_hat = host[3];
     out->max_div_B = host[4];
     out->max_B_hat = host[5];
-    return PSATD_OK;
+    return check_device_error(c);
 }
 
 double psatd_time(const psatd_ctx* c) { return c ? c->t : 0.0; }
@@ -664,14 +772,23 @@ psatd_status psatd_synchronize(psatd_ctx* c) {
     psatd_status st = check_ctx(c, false);
     if (st) return st;
     CK(c, cudaStreamSynchronize(c->stream));
-    return PSATD_OK;
+    return check_device_error(c);
 }
 
 long long psatd_launch_count(const psatd_ctx* c) { return c ? c->launches : 0; }
 
+psatd_status psatd_selftest_wait_timeout(psatd_ctx* c) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    CK(c, launch_wait_timeout_selftest(c->dev_err, c->stream));
+    ++c->launches;
+    return psatd_synchronize(c);
+}
+
 psatd_status psatd_set_kernel_path(psatd_ctx* c, int path) {
     if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
-    if (path != PSATD_PATH_AUTO && path != PSATD_PATH_GENERIC) return fail(c, PSATD_ERR_ARG, "unknown kernel path");
+    if (path != PSATD_PATH_AUTO && path != PSATD_PATH_GENERIC && path != PSATD_PATH_REGISTER)
+        return fail(c, PSATD_ERR_ARG, "unknown kernel path");
     c->kernel_path = path;
     return PSATD_OK;
 }

@@ -27,9 +27,9 @@ EXPORTS = (
     "psatd_sample_focal_plane", "psatd_diagnostics", "psatd_time", "psatd_set_time",
     "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
     "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
-    "psatd_set_kernel_path",
+    "psatd_set_kernel_path", "psatd_selftest_wait_timeout",
 )
-PATH_AUTO, PATH_GENERIC = 0, 1
+PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
 KERNEL_KINDS = ("fft_x", "fft_y", "fft_z", "kspace_z", "init_pulse", "sample_plane", "diagnostics",
                 "plane_xy")
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
         "psatd_kernel_name": (C.c_char_p, [C.c_int]),
         "psatd_set_kernel_path": (C.c_int, [P, C.c_int]),
+        "psatd_selftest_wait_timeout": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

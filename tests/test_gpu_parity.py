@@ -291,7 +291,7 @@ def test_fast_kernels_match_oracle_and_generic(lib, prec, shape):
     f = W.random_complex_field((6, Nz, Ny, Nx), seed=Nx * 3 + Ny + Nz)
     dt = 0.41
     out = {}
-    for path in (lib.PATH_AUTO, lib.PATH_GENERIC):
+    for path in (lib.PATH_AUTO, lib.PATH_REGISTER, lib.PATH_GENERIC):
         with lib.Context(g, None, dt, prec) as ctx:
             ctx.set_kernel_path(path)
             ctx.set_fields(f)
@@ -306,3 +306,47 @@ def test_fast_kernels_match_oracle_and_generic(lib, prec, shape):
         assert rel(out[path][0], F_ref) <= TOL[prec]
         assert rel(out[path][1], step_ref) <= 2 * TOL[prec]
     assert rel(out[lib.PATH_AUTO][1], out[lib.PATH_GENERIC][1]) <= 2 * TOL[prec]
+    assert rel(out[lib.PATH_REGISTER][1], out[lib.PATH_GENERIC][1]) <= 2 * TOL[prec]
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(lib):
+    import ctypes as C
+    g = W.plain_grid(64)
+    f0 = W.random_divfree_field(g, 5)
+    with lib.Context(g, None, g.courant_dt(), 32) as ctx:
+        st = lib.lib().psatd_selftest_wait_timeout(ctx._ptr)
+        assert st == lib.ERR_TIMEOUT
+        assert b"bounded device wait" in lib.lib().psatd_last_error(ctx._ptr)
+        ctx.synchronize()                       # error word was cleared
+        ctx.set_fields(f0)
+        ctx.advance(2)
+        got = ctx.get_field(-1)
+    assert rel(got, O.advance(f0, ogrid(g), g.courant_dt(), 2)) <= TOL[32]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("Nz", [6, 64])
+def test_plane_cluster_kernel_256_planes(lib, prec, Nz):
+    """256 x 256 planes (the cluster x+y kernel in FP32) against the oracle and
+    the per-axis kernels, for a thin, a fast-z and the full-size z extent."""
+    g = W.GridSpec(256, 256, Nz, 0.5, 0.7, 0.3, 0.0, 0.0, 0.0, 1.0)
+    f = W.random_complex_field((6, Nz, 256, 256), seed=Nz)
+    dt = 0.29
+    res = {}
+    for path in (lib.PATH_AUTO, lib.PATH_REGISTER):
+        with lib.Context(g, None, dt, prec) as ctx:
+            ctx.set_kernel_path(path)
+            ctx.set_fields(f)
+            ctx.fft(lib.FORWARD)
+            F = ctx.get_field(-1)
+            ctx.fft(lib.INVERSE)
+            back = ctx.get_field(-1) / g.cells
+            ctx.set_fields(f)
+            ctx.advance(1)
+            res[path] = (F, back, ctx.get_field(-1))
+    F_ref = O.fft3(f)
+    step_ref = O.advance(f, ogrid(g), dt, 1)
+    for path, (F, back, st) in res.items():
+        assert rel(F, F_ref) <= TOL[prec]
+        assert rel(back, f) <= TOL[prec]
+        assert rel(st, step_ref) <= TOL[prec]
