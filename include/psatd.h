@@ -200,6 +200,24 @@ psatd_status psatd_set_kernel_path(psatd_ctx* ctx, int path);
  * context stays usable afterwards.  The paper has no counterpart. */
 psatd_status psatd_selftest_wait_timeout(psatd_ctx* ctx);
 
+/* Energy sums (|E|^2 and |B|^2 over all cells, float64) of a six-component field
+ * in the storage layout above, for callers that cannot allocate device memory
+ * when they need it: during CUDA graph capture, under a framework allocator
+ * that has reserved the whole device, or in loops where cudaMalloc/cudaFree
+ * (which may synchronise the device) are not acceptable.  It allocates nothing:
+ * its partial sums live in a 1 MB array compiled into the library, so n_cells
+ * must be 1..2^30 (else PSATD_ERR_SIZE).  fields is a device pointer to
+ * 6 * n_cells complex values of the given precision (32 or 64); out receives
+ * {energy_E, energy_B}, on the device (out_on_device != 0, asynchronous on
+ * cuda_stream) or on the host (the call then synchronises the stream).  The
+ * first call on each device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  All calls share
+ * the array, so calls that overlap on the GPU race and must be serialised by the
+ * caller.  Needs no context; errors are returned only as the status.  The paper
+ * has no counterpart. */
+psatd_status psatd_energy_noalloc(const void* fields, int precision, long long n_cells, double* out,
+                                  int out_on_device, void* cuda_stream);
+
 /* Kernel kinds for per-kernel timing. */
 enum {
     PSATD_KERNEL_FFT_X = 0,      /* generic FFT along x */

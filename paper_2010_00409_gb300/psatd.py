@@ -27,7 +27,7 @@ EXPORTS = (
     "psatd_sample_focal_plane", "psatd_diagnostics", "psatd_time", "psatd_set_time",
     "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
     "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
-    "psatd_set_kernel_path", "psatd_selftest_wait_timeout",
+    "psatd_set_kernel_path", "psatd_selftest_wait_timeout", "psatd_energy_noalloc",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_kernel_name": (C.c_char_p, [C.c_int]),
         "psatd_set_kernel_path": (C.c_int, [P, C.c_int]),
         "psatd_selftest_wait_timeout": (C.c_int, [P]),
+        "psatd_energy_noalloc": (C.c_int, [P, C.c_int, C.c_longlong, C.POINTER(C.c_double), C.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
