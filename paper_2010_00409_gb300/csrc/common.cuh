@@ -100,11 +100,13 @@ cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>
 
 // Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
 // 8-byte elements {Nx * sizeof(complex)/8, Ny, Nz, 6} with box
-// {kspace_tma_box_x(prec), 1, Nz, 1}.  Device errors are OR-ed into *err.
+// {kspace_tma_box_x(prec), 1, kspace_tma_box_z(Nz), 1}.  Device errors are OR-ed
+// into *err.
 template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
                               int* err, cudaStream_t s);
 int kspace_tma_box_x(int prec);
+int kspace_tma_box_z(int Nz);
 cudaError_t launch_wait_timeout_selftest(int* err, cudaStream_t s);
 
 // Fused x+y FFT of x-y planes through a thread-block cluster (distributed

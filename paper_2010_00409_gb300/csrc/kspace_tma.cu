@@ -17,18 +17,29 @@ namespace psatd {
 
 namespace {
 
+// Shared-memory layout of one component slot: element (row k1, lane j, column c)
+// at k1*RP + j*W + c with RP = N2*W, i.e. the dense [z][c] tile the copy engine
+// writes (z = N2 k1 + j).  Every copy destination is a whole slot, so it keeps
+// the 128-byte alignment bulk-tensor copies require.
+//   - raw element z = j + N2 n1 of column c sits at (n1, j): thread (c, j) reads
+//     exactly the positions it later scatters to;
+//   - the spectrum a thread holds after the forward transform (register
+//     r = q N2 + k2 <-> kz = (t + N2 q) + N1 k2) is stored back at the same
+//     positions (r, t), so the per-mode update and the first read of the inverse
+//     touch only the thread's own positions and need no barrier.
 template <typename T, int N1, int N2, int W>
 __global__ void __launch_bounds__(W * N2)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
                   const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
                   const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err) {
     constexpr int Nz = N1 * N2;
-    constexpr int RS = N2 * W, ES = W;
-    constexpr int SLOT = Nz * W;
-    constexpr uint32_t kBytes = 6u * SLOT * sizeof(cplx<T>);
+    constexpr int RP = N2 * W;
+    constexpr int SLOT = N1 * RP;
+    constexpr int NB = sizeof(T) == 4 ? 2 : 1;                 // components per exchange round
+    constexpr uint32_t kBytes = 6u * Nz * W * sizeof(cplx<T>);
     static_assert(kBytes < (1u << 20), "mbarrier transaction count is 20 bits");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    cplx<T>* spec = reinterpret_cast<cplx<T>*>(smem_raw);      // [6][Nz][W]
+    cplx<T>* spec = reinterpret_cast<cplx<T>*>(smem_raw);      // [6][N1][RP]
     __shared__ __align__(8) uint64_t bar;
     __shared__ int failed;
 
@@ -49,6 +60,29 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         mbar_arrive_expect_tx(&bar, kBytes);
         constexpr int xw = (int)(sizeof(cplx<T>) / 8);        // 8-byte elements per complex
         for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
+    }
+
+    // while the copies fly: outer twiddles W_N^{j k1} (the inverse uses their
+    // conjugates with k1 = j) and the per-mode coefficients of this thread's modes
+    cplx<T> twr[N1];
+    static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
+    const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
+    const int ax = min(ix, Nx - ix), ay = min(y, Ny - y);
+    const T kx = kxs[ix], ky = kys[y];
+    ModeCoef<T> mc[N1];
+    T kzr[N1];
+    static_for<0, N1 / N2>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        static_for<0, N2>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            const int iz = (j + N2 * q) + N1 * k2;
+            const int az = min(iz, Nz - iz);
+            mc[q * N2 + k2] = coef[((size_t)az * Nyh + ay) * Nxh + ax];
+            kzr[q * N2 + k2] = kzs[iz];
+        });
+    });
+
+    if (threadIdx.x == 0) {
         bool ok = mbar_wait_bounded(&bar, 0);
         if (!ok) {
             atomicOr(err, DEV_ERR_TMA_TIMEOUT);
@@ -59,64 +93,100 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     __syncthreads();
     if (failed) return;
 
+    cplx<T>* own = spec + j * W + c;                           // (row r, this thread) at own[r * RP]
+    cplx<T> v[NB][N1];
+
+    // forward z transforms, NB components per exchange round
+#pragma unroll 1
+    for (int q0 = 0; q0 < 6; q0 += NB) {
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            cplx<T>* sl = own + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto nc) { v[b][decltype(nc)::value] = sl[decltype(nc)::value * RP]; });
+            reg_dft<T, -1, N1>(v[b]);
+            static_for<1, N1>([&](auto kc) {
+                constexpr int k1 = decltype(kc)::value;
+                if (j) v[b][k1] = cmul(v[b][k1], twr[k1]);
+            });
+            static_for<0, N1>([&](auto kc) { sl[decltype(kc)::value * RP] = v[b][decltype(kc)::value]; });
+        });
+        __syncthreads();
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            const cplx<T>* sl = spec + (q0 + b) * SLOT + c;
+            static_for<0, N1 / N2>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                cplx<T> w[N2];
+                const cplx<T>* row = sl + (j + N2 * q) * RP;
+                static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value * W]; });
+                reg_dft<T, -1, N2>(w);
+                static_for<0, N2>([&](auto kc) { v[b][q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
+            });
+        });
+        __syncthreads();
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            cplx<T>* sl = own + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto rc) { sl[decltype(rc)::value * RP] = v[b][decltype(rc)::value]; });
+        });
+    }
+
+    // per-mode update on the thread's own modes (no barrier needed)
+    static_for<0, N1>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        cplx<T>* o = own + r * RP;
+        cplx<T> Ex = o[0], Ey = o[SLOT], Ez = o[2 * SLOT];
+        cplx<T> Bx = o[3 * SLOT], By = o[4 * SLOT], Bz = o[5 * SLOT];
+        const ModeCoef<T> m = mc[r];
+        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S);
+        o[0] = Ex; o[SLOT] = Ey; o[2 * SLOT] = Ez;
+        o[3 * SLOT] = Bx; o[4 * SLOT] = By; o[5 * SLOT] = Bz;
+    });
+
+    // inverse z transforms, NB components per exchange round
     cplx<T>* base = data + (size_t)y * Nx + ix;
-    cplx<T> v[N1];
-
-    // forward z transforms; raw element (z, c) sits at z*W + c of its slot and
-    // each thread's exchange writes land on exactly the positions it read
-    for (int q = 0; q < 6; ++q) {
-        cplx<T>* sl = spec + q * SLOT + c;
-        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = sl[(j + N2 * decltype(nc)::value) * W]; });
-        stage_a_fwd<T, -1, N1, N2>(v, j, tw);
-        xscatter<T, N1, N2, RS, ES>(v, sl, j);
-        __syncthreads();
-        xgather_fwd<T, -1, N1, N2, RS, ES>(v, sl, j);
-        __syncthreads();
-        static_for<0, N1 / N2>([&](auto qc) {
-            constexpr int qq = decltype(qc)::value;
-            static_for<0, N2>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                sl[((j + N2 * qq) + N1 * k2) * W] = v[qq * N2 + k2];
-            });
+#pragma unroll 1
+    for (int q0 = 0; q0 < 6; q0 += NB) {
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            const cplx<T>* sl = own + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto rc) { v[b][decltype(rc)::value] = sl[decltype(rc)::value * RP]; });
         });
-    }
-    __syncthreads();
-
-    {
-        const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
-        const int ax = min(ix, Nx - ix), ay = min(y, Ny - y);
-        const T kx = kxs[ix], ky = kys[y];
-        cplx<T>* sl = spec + c;
-#pragma unroll 4
-        for (int s = 0; s < N1; ++s) {
-            const int iz = j + N2 * s;
-            const int az = min(iz, Nz - iz);
-            const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
-            const int o = iz * W;
-            cplx<T> Ex = sl[o], Ey = sl[SLOT + o], Ez = sl[2 * SLOT + o];
-            cplx<T> Bx = sl[3 * SLOT + o], By = sl[4 * SLOT + o], Bz = sl[5 * SLOT + o];
-            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzs[iz] * m.kinv, m.C, m.S);
-            sl[o] = Ex; sl[SLOT + o] = Ey; sl[2 * SLOT + o] = Ez;
-            sl[3 * SLOT + o] = Bx; sl[4 * SLOT + o] = By; sl[5 * SLOT + o] = Bz;
-        }
-    }
-    __syncthreads();
-
-    for (int q = 0; q < 6; ++q) {
-        cplx<T>* sl = spec + q * SLOT + c;
-        static_for<0, N1 / N2>([&](auto qc) {
-            constexpr int qq = decltype(qc)::value;
-            static_for<0, N2>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                v[qq * N2 + k2] = sl[((j + N2 * qq) + N1 * k2) * W];
+        __syncthreads();
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            cplx<T>* sl = spec + (q0 + b) * SLOT + c;
+            static_for<0, N1 / N2>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                cplx<T> w[N2];
+                static_for<0, N2>([&](auto kc) { w[decltype(kc)::value] = v[b][q * N2 + decltype(kc)::value]; });
+                reg_dft<T, +1, N2>(w);
+                const int k1 = j + N2 * q;
+                cplx<T>* row = sl + k1 * RP;
+                static_for<0, N2>([&](auto nc) {
+                    constexpr int n2 = decltype(nc)::value;
+                    cplx<T> val = w[n2];
+                    if (n2 > 0 && k1 > 0) {
+                        // W_N^{-n2 k1}; for q = 0 this is conj(twr[n2]) (k1 = j)
+                        const cplx<T> tv = (q == 0) ? twr[n2] : tw[n2 * k1];
+                        val = cmulc(val, tv);
+                    }
+                    row[n2 * W] = val;
+                });
             });
         });
         __syncthreads();
-        xscatter_inv<T, +1, N1, N2, RS, ES>(v, sl, j, tw);
-        __syncthreads();
-        xgather_inv<T, +1, N1, N2, RS, ES>(v, sl, j);
-        cplx<T>* p = base + q * cstride;
-        static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[decltype(nc)::value]; });
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            const cplx<T>* sl = own + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto kc) { v[b][decltype(kc)::value] = sl[decltype(kc)::value * RP]; });
+        });
+        static_for<0, NB>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            reg_dft<T, +1, N1>(v[b]);
+            cplx<T>* p = base + (q0 + b) * cstride;
+            static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
+        });
     }
 }
 
@@ -171,6 +241,9 @@ cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridG
 }
 
 int kspace_tma_box_x(int prec) { return prec == 64 ? kspace_tma_width<double>() * 2 : kspace_tma_width<float>(); }
+
+// z-extent of one copy box: the whole pencil (0 if Nz has no plan here)
+int kspace_tma_box_z(int Nz) { return (Nz == 64 || Nz == 128 || Nz == 256) ? Nz : 0; }
 
 template cudaError_t launch_kspace_tma<float>(const CUtensorMap&, cplx<float>*, const GridGeom&, const Tables<float>&, int*, cudaStream_t);
 template cudaError_t launch_kspace_tma<double>(const CUtensorMap&, cplx<double>*, const GridGeom&, const Tables<double>&, int*, cudaStream_t);

@@ -296,7 +296,9 @@ bool ensure_field_map(psatd_ctx* c) {
     const cuuint64_t dims[4] = {(cuuint64_t)g.Nx * xw, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, 6};
     const cuuint64_t strides[3] = {(cuuint64_t)g.Nx * es, (cuuint64_t)g.Nx * g.Ny * es,
                                    (cuuint64_t)g.Nx * g.Ny * g.Nz * es};
-    const cuuint32_t box[4] = {(cuuint32_t)kspace_tma_box_x(c->prec), 1, (cuuint32_t)g.Nz, 1};
+    const int bz = kspace_tma_box_z(g.Nz);
+    if (bz == 0) return false;
+    const cuuint32_t box[4] = {(cuuint32_t)kspace_tma_box_x(c->prec), 1, (cuuint32_t)bz, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     if (dims[0] < box[0] || (g.Nx * es) % 16 != 0) return false;
     CUresult r = enc(&c->field_map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, c->fields, dims, strides, box, estr,

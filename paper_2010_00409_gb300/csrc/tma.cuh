@@ -1,6 +1,8 @@
 // Thin inline-PTX wrappers for the Blackwell bulk-tensor copy engine (TMA) and
 // shared-memory mbarriers.  Loads are plain tiled copies into this CTA's own
-// shared memory (no multicast).
+// shared memory (no multicast).  A tiled copy's shared-memory destination must
+// be 128-byte aligned and its innermost global coordinate times the element size
+// a multiple of 16 bytes.
 #pragma once
 
 #include <cuda.h>
