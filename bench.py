@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+from paper_2010_00409_gb300 import replicas as RP  # noqa: E402
 from paper_2010_00409_gb300 import workloads as W  # noqa: E402
 
 METRIC = "PSATD cell-steps/s"
@@ -52,10 +53,7 @@ def args_parse():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return RP.env()
 
 
 def measured_peaks():
@@ -196,10 +194,7 @@ def run_ours(a):
         job(ctx, out_dev)
     ctx.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = RP.barrier
 
     uuid = None
     try:
@@ -225,14 +220,8 @@ def run_ours(a):
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     clk = clocks.stop()
-    t_max = t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    cell_steps = g.cells * n_steps * a.steps * world
-    value = cell_steps / (t_max / 1e3)
+    t_max = RP.max_over_ranks(t_ms, device=dev)
+    value = RP.whole_job_rate(g.cells * n_steps * a.steps, world, t_max / 1e3)
 
     # roofline of the dominant per-step kernel: algorithmic bytes = one read and one
     # write of the six complex64 components (96 B per cell) per launch
@@ -271,6 +260,8 @@ def run_ours(a):
         line["e2e"] = e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world)
     if not a.no_fp64:
         line["fp64"] = fp64_measure(g, m, p, n_steps, dt, dev, stream)
+        line["focal_forms"] = focal_forms(ctx, g, m, p, n_steps, plane, dt, dev, stream, out_dev,
+                                          line["fp64"]["ms_per_psatd_step"])
     ctx.close()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cells, times, sample = oracle_sample_rate(a.size, reps=1)
@@ -338,6 +329,46 @@ def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
         prof = c.profile_read()
     return {"value": g.cells * n / (ms / 1e3), "unit": UNIT, "psatd_steps": n, "ms_per_psatd_step": ms / n,
             "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()}}
+
+
+def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_step64, reps=5):
+    """Focal fields/s of the stepped FP32 job (just timed), the FP32 and FP64
+    one-shot paths (one exact step of T = R0/c, sampled from the spectrum) and the
+    plain FP64 stepped solver (from its measured step time), each with the relative
+    L2 error of its focal plane against the FP64 one-shot plane."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    T = n_steps * dt
+    args = (plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])
+    res = {}
+    with psatd.Context(g, m, dt, 64, stream=stream) as c64:
+        out64 = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex128, device=dev)
+        c64.focal_one_shot(p, T, *args, out=out64)
+        c64.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            c64.focal_one_shot(p, T, *args, out=out64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ref = out64.cpu().numpy()
+        res["one_shot_fp64"] = {"focal_fields_per_s": reps / (e0.elapsed_time(e1) / 1e3), "rel_l2_err_vs_fp64": 0.0}
+    nref = float(np.linalg.norm(ref))
+    res["stepped_fp32"] = {"rel_l2_err_vs_fp64": float(np.linalg.norm(stepped32.cpu().numpy() - ref) / nref)}
+    out32 = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
+    ctx32.focal_one_shot(p, T, *args, out=out32)
+    ctx32.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx32.focal_one_shot(p, T, *args, out=out32)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    res["one_shot_fp32"] = {"focal_fields_per_s": reps / (e0.elapsed_time(e1) / 1e3),
+                            "rel_l2_err_vs_fp64": float(np.linalg.norm(out32.cpu().numpy() - ref) / nref)}
+    res["stepped_fp64_estimate"] = {"focal_fields_per_s": 1e3 / (ms_step64 * n_steps),
+                                    "note": "from the measured FP64 PSATD step time x %d steps" % n_steps}
+    return res
 
 
 def main():

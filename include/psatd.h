@@ -159,6 +159,20 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* ctx, double x_phys, int ny, int
                                       double y0, double y1, double z0, double z1,
                                       int comp_mask, void* dst, int dst_on_device);
 
+/* One-shot focal field (the solver is exact in time in vacuum, Sec. 2.1 and the
+ * single step of Delta t = R0/c of Sec. 3.1): initialise the pulse (as
+ * psatd_init_pulse, including its div_project), advance by ONE step of size T,
+ * and sample the plane x = x_phys at time T exactly as psatd_sample_focal_plane,
+ * evaluating the interpolant straight from the updated spectrum (no inverse 3D
+ * transform).  Afterwards the field storage holds that spectrum, so advance,
+ * fft, diagnostics and sample_focal_plane return PSATD_ERR_STATE until a pulse
+ * or all six components are set again; psatd_time() is T.  The coefficient
+ * table for T is built on the host (float64) and cached for the next call with
+ * the same T. */
+psatd_status psatd_focal_one_shot(psatd_ctx* ctx, const psatd_pulse* pulse, double T, double x_phys,
+                                  int ny, int nz, double y0, double y1, double z0, double z1,
+                                  int comp_mask, void* dst, int dst_on_device);
+
 /* Energy and spectral divergence of the current fields (float64 accumulation).
  * Synchronises. */
 psatd_status psatd_diagnostics(psatd_ctx* ctx, psatd_diag* out);

@@ -78,8 +78,13 @@ template <typename T> struct Tables {
     AxisPlan plan[3];
 };
 
-// K2 modes
-enum KspaceMode { KS_ROTATE = 0, KS_PROJECT = 1 };
+// K2 modes: ROTATE = full step (forward z, update, inverse z); PROJECT = the
+// one-time transverse projection; ROTATE_SPECTRAL = forward z and update only,
+// leaving the spectrum (natural kx, ky, kz order) in storage.
+// KS_ROTATE_SPECTRAL_PROJ also removes the longitudinal part of B before the
+// update (E's is removed by Eq. 3 itself, and k^ x B does not see it), which
+// equals the one-time projection followed by the update.
+enum KspaceMode { KS_ROTATE = 0, KS_PROJECT = 1, KS_ROTATE_SPECTRAL = 2, KS_ROTATE_SPECTRAL_PROJ = 3 };
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (one translation unit each); all return cudaGetLastError().
@@ -104,7 +109,7 @@ cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>
 // into *err.
 template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s);
+                              int* err, cudaStream_t s, bool spectral_out = false, bool project_b = false);
 int kspace_tma_box_x(int prec);
 int kspace_tma_box_z(int Nz);
 cudaError_t launch_wait_timeout_selftest(int* err, cudaStream_t s);
@@ -140,7 +145,7 @@ cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const Sh
                                 double x_phys, int ny, int nz, double y0, double y1, double z0,
                                 double z1, double t, const int* comps, int ncomp,
                                 const SampleScratch& sc, cplx<T>* out, cudaStream_t s,
-                                long long* nlaunch);
+                                long long* nlaunch, bool from_spectrum = false);
 
 // Diagnostics: energy partials and spectral divergence partials.
 template <typename T>

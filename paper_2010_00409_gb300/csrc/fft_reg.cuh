@@ -294,7 +294,14 @@ __device__ __forceinline__ void xgather_inv(cplx<T> (&v)[N1], const cplx<T>* sc,
 // n = k/|k| (0 at k = 0):  E <- C'(E - n(n.E)) + i S' n x B,  B <- C' B - i S' n x E.
 template <typename T>
 __device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& Ez, cplx<T>& Bx,
-                                            cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, T C, T S) {
+                                            cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, T C, T S,
+                                            bool project_b = false) {
+    if (project_b) {
+        const T kBr = nx * Bx.x + ny * By.x + nz * Bz.x, kBi = nx * Bx.y + ny * By.y + nz * Bz.y;
+        Bx = mk<T>(Bx.x - nx * kBr, Bx.y - nx * kBi);
+        By = mk<T>(By.x - ny * kBr, By.y - ny * kBi);
+        Bz = mk<T>(Bz.x - nz * kBr, Bz.y - nz * kBi);
+    }
     const T kEr = nx * Ex.x + ny * Ey.x + nz * Ez.x, kEi = nx * Ex.y + ny * Ey.y + nz * Ez.y;
     const T cBxr = ny * Bz.x - nz * By.x, cBxi = ny * Bz.y - nz * By.y;
     const T cByr = nz * Bx.x - nx * Bz.x, cByi = nz * Bx.y - nx * Bz.y;

@@ -22,7 +22,14 @@ template <typename T>
 __device__ __forceinline__ void mode_update(cplx<T>* F0, cplx<T>* F1, cplx<T>* F2, cplx<T>* F3,
                                             cplx<T>* F4, cplx<T>* F5, T nx, T ny, T nz, T C, T S,
                                             int mode, T scale) {
-    const cplx<T> Ex = *F0, Ey = *F1, Ez = *F2, Bx = *F3, By = *F4, Bz = *F5;
+    const cplx<T> Ex = *F0, Ey = *F1, Ez = *F2;
+    cplx<T> Bx = *F3, By = *F4, Bz = *F5;
+    if (mode == KS_ROTATE_SPECTRAL_PROJ) {
+        const cplx<T> kB = mk<T>(nx * Bx.x + ny * By.x + nz * Bz.x, nx * Bx.y + ny * By.y + nz * Bz.y);
+        Bx = csub(Bx, cscale(kB, nx));
+        By = csub(By, cscale(kB, ny));
+        Bz = csub(Bz, cscale(kB, nz));
+    }
     if (mode == KS_PROJECT) {
         cplx<T> kE = mk<T>(nx * Ex.x + ny * Ey.x + nz * Ez.x, nx * Ex.y + ny * Ey.y + nz * Ez.y);
         cplx<T> kB = mk<T>(nx * Bx.x + ny * By.x + nz * Bz.x, nx * Bx.y + ny * By.y + nz * Bz.y);
@@ -103,7 +110,7 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     }
     __syncthreads();
 
-    if (pl.N > 1) {
+    if (pl.N > 1 && mode != KS_ROTATE_SPECTRAL && mode != KS_ROTATE_SPECTRAL_PROJ) {
         for (int c = 0; c < 6; ++c) {
             cplx<T>* res = fft_tile<T, +1>(F + c * comp_tile, scratch, pl, nw, P, twz);
             if (res != F + c * comp_tile) {

@@ -27,11 +27,12 @@ namespace {
 //     r = q N2 + k2 <-> kz = (t + N2 q) + N1 k2) is stored back at the same
 //     positions (r, t), so the per-mode update and the first read of the inverse
 //     touch only the thread's own positions and need no barrier.
-template <typename T, int N1, int N2, int W>
+template <typename T, int N1, int N2, int W, bool SPECTRAL_OUT>
 __global__ void __launch_bounds__(W * N2)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
                   const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
-                  const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err) {
+                  const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err,
+                  bool project_b) {
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
@@ -138,13 +139,29 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         cplx<T> Ex = o[0], Ey = o[SLOT], Ez = o[2 * SLOT];
         cplx<T> Bx = o[3 * SLOT], By = o[4 * SLOT], Bz = o[5 * SLOT];
         const ModeCoef<T> m = mc[r];
-        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S);
+        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S, project_b);
         o[0] = Ex; o[SLOT] = Ey; o[2 * SLOT] = Ez;
         o[3 * SLOT] = Bx; o[4 * SLOT] = By; o[5 * SLOT] = Bz;
     });
 
-    // inverse z transforms, NB components per exchange round
     cplx<T>* base = data + (size_t)y * Nx + ix;
+    if constexpr (SPECTRAL_OUT) {
+        // store the updated spectrum in natural kz order (one-shot focal path)
+        for (int q = 0; q < 6; ++q) {
+            const cplx<T>* sl = own + q * SLOT;
+            cplx<T>* p = base + q * cstride;
+            static_for<0, N1 / N2>([&](auto qc) {
+                constexpr int qq = decltype(qc)::value;
+                static_for<0, N2>([&](auto kc) {
+                    constexpr int k2 = decltype(kc)::value;
+                    p[(size_t)((j + N2 * qq) + N1 * k2) * plane] = sl[(qq * N2 + k2) * RP];
+                });
+            });
+        }
+        return;
+    }
+
+    // inverse z transforms, NB components per exchange round
 #pragma unroll 1
     for (int q0 = 0; q0 < 6; q0 += NB) {
         static_for<0, NB>([&](auto bc) {
@@ -192,13 +209,14 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
 
 template <typename T, int N1, int N2, int W>
 cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s) {
+                              int* err, cudaStream_t s, bool spectral_out, bool project_b) {
     const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
-    auto k = kspace_tma_kernel<T, N1, N2, W>;
+    auto k = spectral_out ? kspace_tma_kernel<T, N1, N2, W, true> : kspace_tma_kernel<T, N1, N2, W, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((long long)g.Ny * (g.Nx / W));
-    k<<<blocks, W * N2, smem, s>>>(map, data, g.Nx, g.Ny, tb.tw[2], tb.k[0], tb.k[1], tb.k[2], tb.coef, err);
+    k<<<blocks, W * N2, smem, s>>>(map, data, g.Nx, g.Ny, tb.tw[2], tb.k[0], tb.k[1], tb.k[2], tb.coef, err,
+                                   project_b);
     return cudaGetLastError();
 }
 
@@ -229,13 +247,13 @@ template <typename T> constexpr int kspace_tma_width() { return 64 / (int)sizeof
 
 template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s) {
+                              int* err, cudaStream_t s, bool spectral_out, bool project_b) {
     constexpr int W = kspace_tma_width<T>();
     if (g.Nx % W != 0) return cudaErrorNotSupported;
     switch (g.Nz) {
-        case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s);
-        case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s);
-        case 256: return kspace_tma_launch<T, 16, 16, W>(map, data, g, tb, err, s);
+        case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s, spectral_out, project_b);
+        case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s, spectral_out, project_b);
+        case 256: return kspace_tma_launch<T, 16, 16, W>(map, data, g, tb, err, s, spectral_out, project_b);
         default: return cudaErrorNotSupported;
     }
 }
@@ -245,7 +263,7 @@ int kspace_tma_box_x(int prec) { return prec == 64 ? kspace_tma_width<double>() 
 // z-extent of one copy box: the whole pencil (0 if Nz has no plan here)
 int kspace_tma_box_z(int Nz) { return (Nz == 64 || Nz == 128 || Nz == 256) ? Nz : 0; }
 
-template cudaError_t launch_kspace_tma<float>(const CUtensorMap&, cplx<float>*, const GridGeom&, const Tables<float>&, int*, cudaStream_t);
-template cudaError_t launch_kspace_tma<double>(const CUtensorMap&, cplx<double>*, const GridGeom&, const Tables<double>&, int*, cudaStream_t);
+template cudaError_t launch_kspace_tma<float>(const CUtensorMap&, cplx<float>*, const GridGeom&, const Tables<float>&, int*, cudaStream_t, bool, bool);
+template cudaError_t launch_kspace_tma<double>(const CUtensorMap&, cplx<double>*, const GridGeom&, const Tables<double>&, int*, cudaStream_t, bool, bool);
 
 }  // namespace psatd

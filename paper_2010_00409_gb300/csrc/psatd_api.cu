@@ -79,6 +79,13 @@ struct psatd_ctx {
     void* field_map_ptr = nullptr;      // storage the map was encoded for
     bool field_map_ok = false;
     int* dev_err = nullptr;             // device error word (bits of psatd::DeviceError)
+
+    // one-shot focal path: coefficient table for one step of T, and a flag set
+    // while the field storage holds an updated spectrum instead of the field
+    DevBuf coef_T;
+    double coef_T_step = 0.0;
+    bool coef_T_ok = false;
+    bool holds_spectrum = false;
     std::string err = "no error";
 
     // per-kernel event timing (psatd_profile_enable)
@@ -178,7 +185,8 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
 
 // (C/Ntot, S/Ntot, 1/|k|) per |m| octant, float64 then rounded once.
 template <typename T>
-psatd_status upload_coef(psatd_ctx* c, double dt) {
+psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr) {
+    DevBuf& buf = dst ? *dst : c->coef;
     const psatd_grid& g = c->grid;
     const int hx = g.Nx / 2 + 1, hy = g.Ny / 2 + 1, hz = g.Nz / 2 + 1;
     const double ntot = (double)n_cells(g);
@@ -200,8 +208,8 @@ psatd_status upload_coef(psatd_ctx* c, double dt) {
         }
     }
     const size_t bytes = tab.size() * sizeof(ModeCoef<T>);
-    CK(c, ensure_buf(c->coef, bytes));
-    CK(c, cudaMemcpyAsync(c->coef.p, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(c, ensure_buf(buf, bytes));
+    CK(c, cudaMemcpyAsync(buf.p, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return PSATD_OK;
 }
@@ -210,9 +218,11 @@ psatd_status set_coef(psatd_ctx* c, double dt) {
     return c->prec == 64 ? upload_coef<double>(c, dt) : upload_coef<float>(c, dt);
 }
 
-psatd_status check_ctx(psatd_ctx* c, bool need_fields) {
+psatd_status check_ctx(psatd_ctx* c, bool need_fields, bool need_physical = false) {
     if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
     if (need_fields && !c->fields) return fail(c, PSATD_ERR_STATE, "no field storage bound");
+    if (need_physical && c->holds_spectrum)
+        return fail(c, PSATD_ERR_STATE, "storage holds the one-shot spectrum; set the field or a pulse first");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     return PSATD_OK;
@@ -422,6 +432,36 @@ double F_series(double t0) {
 
 }  // namespace
 
+namespace {
+
+// Forward x+y transform, then the k-space pass with the table of one step T that
+// leaves the updated spectrum (with 1/N folded in) in storage.
+template <typename T>
+cudaError_t one_shot_spectrum(psatd_ctx* c, bool project_b) {
+    const GridGeom g = geom(c);
+    Tables<T> tb = tables<T>(c);
+    tb.coef = static_cast<const ModeCoef<T>*>(c->coef_T.p);
+    cplx<T>* f = static_cast<cplx<T>*>(c->fields);
+    cudaError_t e = plane_xy<T>(c, f, 6, -1, -1);
+    if (e == cudaErrorNotSupported) {
+        if ((e = fft_axis<T>(c, f, 6, 0, -1, -1)) != cudaSuccess) return e;
+        e = fft_axis<T>(c, f, 6, 1, -1, -1);
+    }
+    if (e != cudaSuccess) return e;
+    return timed(c, PSATD_KERNEL_KSPACE, [&] {
+        ++c->launches;
+        if (c->kernel_path == PSATD_PATH_AUTO && ensure_field_map(c)) {
+            cudaError_t r = launch_kspace_tma<T>(c->field_map, f, g, tb, c->dev_err, c->stream, true, project_b);
+            if (r != cudaErrorNotSupported) return r;
+        }
+        --c->launches;
+        return launch_kspace_z<T>(f, g, tb, project_b ? KS_ROTATE_SPECTRAL_PROJ : KS_ROTATE_SPECTRAL, 0.0,
+                                  c->stream, &c->launches);
+    });
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* psatd_status_string(psatd_status s) {
@@ -522,6 +562,7 @@ void psatd_destroy(psatd_ctx* c) {
     if (c->dev_err) cudaFree(c->dev_err);
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
+    free_buf(c->coef_T);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
@@ -587,7 +628,9 @@ static psatd_status copy_field(psatd_ctx* c, int comp, void* dst, const void* sr
 }
 
 psatd_status psatd_set_field(psatd_ctx* c, int comp, const void* src, int src_on_device) {
-    return copy_field(c, comp, nullptr, src, src_on_device, true);
+    psatd_status st = copy_field(c, comp, nullptr, src, src_on_device, true);
+    if (st == PSATD_OK && comp < 0) c->holds_spectrum = false;
+    return st;
 }
 
 psatd_status psatd_get_field(psatd_ctx* c, int comp, void* dst, int dst_on_device) {
@@ -637,6 +680,7 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
             : launch_init_pulse<float>(static_cast<cplx<float>*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init_pulse launch");
+    c->holds_spectrum = false;
     if (p->div_project) {
         const double scale = 1.0 / (double)n_cells(c->grid);
         e = c->prec == 64 ? spectral_pass<double>(c, KS_PROJECT, scale) : spectral_pass<float>(c, KS_PROJECT, scale);
@@ -646,8 +690,10 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
     return PSATD_OK;
 }
 
+
+
 psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
-    psatd_status st = check_ctx(c, true);
+    psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (n_steps < 0) return fail(c, PSATD_ERR_ARG, "n_steps must be >= 0");
     for (int s = 0; s < n_steps; ++s) {
@@ -660,7 +706,7 @@ psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
 }
 
 psatd_status psatd_fft(psatd_ctx* c, int direction) {
-    psatd_status st = check_ctx(c, true);
+    psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (direction != PSATD_FORWARD && direction != PSATD_INVERSE)
         return fail(c, PSATD_ERR_ARG, "direction must be PSATD_FORWARD or PSATD_INVERSE");
@@ -672,7 +718,7 @@ psatd_status psatd_fft(psatd_ctx* c, int direction) {
 
 psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int nz, double y0, double y1,
                                       double z0, double z1, int comp_mask, void* dst, int dst_on_device) {
-    psatd_status st = check_ctx(c, true);
+    psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
@@ -713,8 +759,68 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
     return PSATD_OK;
 }
 
-psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
+psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double T, double x_phys, int ny,
+                                  int nz, double y0, double y1, double z0, double z1, int comp_mask, void* dst,
+                                  int dst_on_device) {
     psatd_status st = check_ctx(c, true);
+    if (st) return st;
+    if (!is_finite(T)) return fail(c, PSATD_ERR_ARG, "T must be finite");
+    if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
+    if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
+    if (comp_mask <= 0 || comp_mask > 63) return fail(c, PSATD_ERR_ARG, "comp_mask must select 1..6 components");
+    if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
+        return fail(c, PSATD_ERR_ARG, "plane coordinates must be finite");
+    if (!c->coef_T_ok || c->coef_T_step != T) {
+        st = c->prec == 64 ? upload_coef<double>(c, T, &c->coef_T) : upload_coef<float>(c, T, &c->coef_T);
+        if (st) return st;
+        c->coef_T_ok = true;
+        c->coef_T_step = T;
+    }
+    psatd_pulse p = *pulse;
+    const int project = p.div_project;
+    p.div_project = 0;
+    st = psatd_init_pulse(c, &p);
+    if (st) return st;
+    cudaError_t e = c->prec == 64 ? one_shot_spectrum<double>(c, project != 0) : one_shot_spectrum<float>(c, project != 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "one-shot launch");
+    c->holds_spectrum = true;
+    c->t = T;
+    int comps[6], nc = 0;
+    for (int a = 0; a < 6; ++a)
+        if (comp_mask & (1 << a)) comps[nc++] = a;
+    const psatd_grid& g = c->grid;
+    CK(c, ensure_buf(c->samp_wx, g.Nx * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_wy, (size_t)ny * g.Ny * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_wz, (size_t)nz * g.Nz * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_g, (size_t)nc * g.Nz * g.Ny * sizeof(double2)));
+    CK(c, ensure_buf(c->samp_h, (size_t)nc * g.Nz * ny * sizeof(double2)));
+    const size_t out_bytes = (size_t)nc * nz * ny * cplx_size(c->prec);
+    void* out = dst;
+    if (!dst_on_device) {
+        CK(c, ensure_buf(c->samp_out, out_bytes));
+        out = c->samp_out.p;
+    }
+    SampleScratch sc{static_cast<double2*>(c->samp_wx.p), static_cast<double2*>(c->samp_wy.p),
+                     static_cast<double2*>(c->samp_wz.p), static_cast<double2*>(c->samp_g.p),
+                     static_cast<double2*>(c->samp_h.p)};
+    ShellGeom sh{c->mapping.R0, c->mapping.L};
+    const GridGeom gg = geom(c);
+    e = timed(c, PSATD_KERNEL_SAMPLE, [&] {
+        return c->prec == 64
+            ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, T, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches, true)
+            : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, T, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches, true);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "one-shot sample launch");
+    if (!dst_on_device) {
+        CK(c, cudaMemcpyAsync(dst, out, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return check_device_error(c);
+    }
+    return PSATD_OK;
+}
+
+psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
+    psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (!out) return fail(c, PSATD_ERR_ARG, "NULL out");
     const size_t n = n_cells(c->grid);

@@ -65,6 +65,33 @@ __global__ void weights_kernel(GridGeom g, double x_phys, int ny, int nz, double
     }
 }
 
+// Weights that evaluate the interpolant straight from a spectrum that already
+// carries the 1/N of the inverse DFT (as the k-space pass leaves it):
+// u~(r) = sum_m G(m) prod_a exp(i k_{a,m} (r_a - r_min,a)),  G = F / N.
+__device__ __forceinline__ double2 mode_phase(int i, int N, double d, double s) {
+    const int m = i <= (N - 1) / 2 ? i : i - N;
+    const double ph = 2.0 * kPi * (double)m / (N * d) * s;
+    return make_double2(cos(ph), sin(ph));
+}
+
+__global__ void spectral_weights_kernel(GridGeom g, double x_phys, int ny, int nz, double y0, double y1,
+                                        double z0, double z1, double2* wx, double2* wy, double2* wz) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nwx = g.Nx, nwy = ny * g.Ny, nwz = nz * g.Nz;
+    const double D = g.Nx * g.dx;
+    if (tid < nwx) {
+        double q = (x_phys - g.x_min) / D;
+        const double xt = g.x_min + D * (q - floor(q));              // Eq. 13
+        wx[tid] = mode_phase(tid, g.Nx, g.dx, xt - g.x_min);
+    } else if (tid < nwx + nwy) {
+        const int e = tid - nwx, p = e / g.Ny, j = e - p * g.Ny;
+        wy[e] = mode_phase(j, g.Ny, g.dy, y0 + (y1 - y0) * p / ny - g.y_min);
+    } else if (tid < nwx + nwy + nwz) {
+        const int e = tid - nwx - nwy, q = e / g.Nz, l = e - q * g.Nz;
+        wz[e] = mode_phase(l, g.Nz, g.dz, z0 + (z1 - z0) * q / nz - g.z_min);
+    }
+}
+
 struct CompList { int c[6]; };
 
 // g[a][l][j] = sum_i wx[i] f[c_a][l][j][i]; one warp per (a, l, j) row.
@@ -143,11 +170,14 @@ cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const Sh
                                 double x_phys, int ny, int nz, double y0, double y1, double z0,
                                 double z1, double t, const int* comps, int ncomp,
                                 const SampleScratch& sc, cplx<T>* out, cudaStream_t s,
-                                long long* nlaunch) {
+                                long long* nlaunch, bool from_spectrum) {
     CompList cl;
     for (int a = 0; a < 6; ++a) cl.c[a] = a < ncomp ? comps[a] : 0;
     const int nw = g.Nx + ny * g.Ny + nz * g.Nz;
-    weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
+    if (from_spectrum)
+        spectral_weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
+    else
+        weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
     const long long rows = (long long)ncomp * g.Nz * g.Ny;
     contract_x_kernel<T><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(data, g, cl, ncomp, sc.wx, sc.g);
     const long long nh = (long long)ncomp * g.Nz * ny;
@@ -159,7 +189,7 @@ cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const Sh
     return cudaGetLastError();
 }
 
-template cudaError_t launch_sample_plane<float>(const cplx<float>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<float>*, cudaStream_t, long long*);
-template cudaError_t launch_sample_plane<double>(const cplx<double>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<double>*, cudaStream_t, long long*);
+template cudaError_t launch_sample_plane<float>(const cplx<float>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<float>*, cudaStream_t, long long*, bool);
+template cudaError_t launch_sample_plane<double>(const cplx<double>*, const GridGeom&, const ShellGeom&, double, int, int, double, double, double, double, double, const int*, int, const SampleScratch&, cplx<double>*, cudaStream_t, long long*, bool);
 
 }  // namespace psatd

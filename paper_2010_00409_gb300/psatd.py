@@ -28,6 +28,7 @@ EXPORTS = (
     "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
     "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
     "psatd_set_kernel_path", "psatd_selftest_wait_timeout", "psatd_energy_noalloc",
+    "psatd_focal_one_shot",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -91,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_set_kernel_path": (C.c_int, [P, C.c_int]),
         "psatd_selftest_wait_timeout": (C.c_int, [P]),
         "psatd_energy_noalloc": (C.c_int, [P, C.c_int, C.c_longlong, C.POINTER(C.c_double), C.c_int, P]),
+        "psatd_focal_one_shot": (C.c_int, [P, C.POINTER(PsatdPulse), C.c_double, C.c_double, C.c_int, C.c_int,
+                                           C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +229,22 @@ class Context:
         assert out.dtype == self.dtype and out.is_cuda and out.numel() >= nc * ny * nz
         _check(lib().psatd_sample_focal_plane(self._ptr, x_phys, ny, nz, y0, y1, z0, z1, mask,
                                               C.c_void_p(out.data_ptr()), 1), self._ptr)
+        return out
+
+    def focal_one_shot(self, pulse, T, x_phys, ny, nz, y0, y1, z0, z1, comps=(0, 1, 2), out=None):
+        mask = 0
+        for c in comps:
+            mask |= 1 << c
+        nc = bin(mask).count("1")
+        if out is None:
+            want = np.complex128 if self.precision == 64 else np.complex64
+            out = np.empty((nc, nz, ny), dtype=want)
+            _check(lib().psatd_focal_one_shot(self._ptr, C.byref(make_pulse(pulse)), T, x_phys, ny, nz, y0, y1,
+                                              z0, z1, mask, out.ctypes.data_as(C.c_void_p), 0), self._ptr)
+            return out
+        assert out.dtype == self.dtype and out.is_cuda and out.numel() >= nc * ny * nz
+        _check(lib().psatd_focal_one_shot(self._ptr, C.byref(make_pulse(pulse)), T, x_phys, ny, nz, y0, y1, z0,
+                                          z1, mask, C.c_void_p(out.data_ptr()), 1), self._ptr)
         return out
 
     def diagnostics(self) -> dict:
