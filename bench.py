@@ -49,6 +49,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     return ap.parse_args()
 
 
@@ -263,6 +264,8 @@ def run_ours(a):
         line["focal_forms"] = focal_forms(ctx, g, m, p, n_steps, plane, dt, dev, stream, out_dev,
                                           line["fp64"]["ms_per_psatd_step"])
     ctx.close()
+    if not a.no_sweep:
+        line["batched_sweep"] = sweep_measure(dev, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cells, times, sample = oracle_sample_rate(a.size, reps=1)
         line["cpu_baseline"] = {"value": cells / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -368,6 +371,62 @@ def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_s
                             "rel_l2_err_vs_fp64": float(np.linalg.norm(out32.cpu().numpy() - ref) / nref)}
     res["stepped_fp64_estimate"] = {"focal_fields_per_s": 1e3 / (ms_step64 * n_steps),
                                     "note": "from the measured FP64 PSATD step time x %d steps" % n_steps}
+    return res
+
+
+def sweep_measure(dev, stream, n=64, reps=3, n_check=4):
+    """Batched parameter sweep: n seeded realisations (f-number, CEP, ellipticity)
+    on uneven mapped grids, each one exact step of T = R0/c to its focal plane,
+    all recorded into one CUDA graph and replayed with one launch.  Kernel paths
+    and tile widths per grid shape come from the autotuner.  The FP32 focal planes
+    of the first n_check realisations are compared with FP64 one-shots."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    sweep = W.batched_sweep(n, seed=0)
+    t_setup = time.perf_counter()
+    items = []
+    for g, m, p, T, plane in sweep:
+        c = psatd.Context(g, m, T / 100, 32, stream=stream)
+        c.autotune(2)
+        o = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
+        args = (plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])
+        c.focal_one_shot(p, T, *args, out=o)
+        items.append((c, p, T, args, o))
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+    b = psatd.Batch(stream)
+    with b:
+        for c, p, T, args, o in items:
+            c.focal_one_shot(p, T, *args, out=o)
+    b.launch()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.launch()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    errs = []
+    t64 = 0.0
+    for (g, m, p, T, plane), (c, _, _, args, o) in zip(sweep[:n_check], items[:n_check]):
+        with psatd.Context(g, m, T / 100, 64, stream=stream) as c64:
+            w = c64.focal_one_shot(p, T, *args)
+            c64.synchronize()
+            q0 = time.perf_counter()
+            w = c64.focal_one_shot(p, T, *args)
+            t64 += time.perf_counter() - q0
+        got = o.cpu().numpy()
+        errs.append(float(np.linalg.norm(got - w) / np.linalg.norm(w)))
+    shapes = sorted({(g.Nx, g.Ny, g.Nz) for g, *_ in sweep})
+    res = {"realisations": n, "grid_shapes": len(shapes), "graph_nodes": b.nodes,
+           "focal_fields_per_s": n * reps / (ms / 1e3), "ms_per_graph_launch": ms / reps,
+           "setup_s_incl_autotune": t_setup,
+           "fp64_one_shot_focal_fields_per_s_eager": n_check / t64 if t64 > 0 else None,
+           "max_rel_l2_err_fp32_vs_fp64": max(errs), "err_checked_on": n_check}
+    b.close()
+    for c, *_ in items:
+        c.close()
     return res
 
 

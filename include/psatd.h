@@ -232,6 +232,30 @@ psatd_status psatd_selftest_wait_timeout(psatd_ctx* ctx);
 psatd_status psatd_energy_noalloc(const void* fields, int precision, long long n_cells, double* out,
                                   int out_on_device, void* cuda_stream);
 
+/* Batches: record a sequence of calls on contexts that share one (non-default)
+ * CUDA stream into a CUDA graph and replay it with a single launch, e.g. one
+ * exact step per pulse realisation for parameter sweeps.  Between
+ * psatd_batch_begin and psatd_batch_end (same host thread) only psatd_advance
+ * and psatd_focal_one_shot with a device dst are recorded; calls that need the
+ * host to wait (host copies, diagnostics, set_dt, synchronize,
+ * sample_focal_plane) return PSATD_ERR_STATE, and a one-shot must have run once
+ * outside the capture with the same T and plane size (tables and buffers are
+ * prepared then).  psatd_batch_launch enqueues the graph on the stream and
+ * moves each context's time as the recorded calls would have. */
+typedef struct psatd_batch psatd_batch;
+psatd_status psatd_batch_begin(void* cuda_stream, psatd_batch** out);
+psatd_status psatd_batch_end(psatd_batch* batch);
+psatd_status psatd_batch_launch(psatd_batch* batch);
+long long psatd_batch_nodes(const psatd_batch* batch);      /* graph nodes, 0 if none */
+void psatd_batch_destroy(psatd_batch* batch);
+
+/* Autotuner: times trial_steps PSATD steps of each kernel path (AUTO, REGISTER,
+ * GENERIC) and generic tile width scale (1/2, 1, 2) on a scratch copy of the
+ * field, keeps the fastest for this context and caches it per grid shape and
+ * precision for the process (later calls for the same shape apply the cached
+ * choice without timing and report ms_per_step = -1).  Outputs may be NULL. */
+psatd_status psatd_autotune(psatd_ctx* ctx, int trial_steps, int* path, int* tile_shift, double* ms_per_step);
+
 /* Kernel kinds for per-kernel timing. */
 enum {
     PSATD_KERNEL_FFT_X = 0,      /* generic FFT along x */

@@ -76,6 +76,7 @@ template <typename T> struct Tables {
     const T* k[3];              // k_a[i] = 2 pi m(i) / (N_a d_a)
     const ModeCoef<T>* coef;    // (Nz/2+1) x (Ny/2+1) x (Nx/2+1)
     AxisPlan plan[3];
+    int tile_shift = 0;         // generic kernels: tile width scaled by 2^tile_shift (autotuner)
 };
 
 // K2 modes: ROTATE = full step (forward z, update, inverse z); PROJECT = the

@@ -71,12 +71,14 @@ fft_axis_kernel(cplx<T>* __restrict__ data, int axis, int Nx, int Ny, int Nz, in
 // of the tile; x takes enough rows for ~2048 elements.  Shared memory is
 // capped at 96 KB so two blocks fit on an SM.
 template <typename T>
-void choose_tile(int axis, int N, int Nx, int* W, int* P) {
+void choose_tile(int axis, int N, int Nx, int shift, int* W, int* P) {
     const int es = (int)sizeof(cplx<T>);
     *P = N + 1;
     int w;
     if (axis == 0) w = max(1, min(64, 2048 / max(N, 1)));
     else w = min(Nx, 128 / es);
+    if (shift > 0) w = min(axis == 0 ? 128 : Nx, w << shift);
+    if (shift < 0) w = max(1, w >> -shift);
     while (w > 1 && 2 * (size_t)w * (*P) * es > 96 * 1024) w /= 2;
     *W = max(1, w);
 }
@@ -90,7 +92,7 @@ cudaError_t launch_fft_axis(cplx<T>* data, int ncomp, const GridGeom& g, const T
     if (pl.N <= 1) return cudaSuccess;
     int W, P;
     const int Nx = g.Nx;
-    choose_tile<T>(axis, pl.N, Nx, &W, &P);
+    choose_tile<T>(axis, pl.N, Nx, tb.tile_shift, &W, &P);
     long long nblocks;
     if (axis == 0) nblocks = ((long long)ncomp * g.Nz * g.Ny + W - 1) / W;
     else nblocks = (long long)ncomp * (axis == 1 ? g.Nz : g.Ny) * ((Nx + W - 1) / W);

@@ -136,6 +136,8 @@ cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& t
     const int es = (int)sizeof(cplx<T>);
     const int P = g.Nz + 1;
     int W = min(g.Nx, 128 / es);
+    if (tb.tile_shift > 0) W = min(g.Nx, W << tb.tile_shift);
+    if (tb.tile_shift < 0) W = max(1, W >> -tb.tile_shift);
     while (W > 1 && 7 * (size_t)W * P * es > 200 * 1024) W /= 2;
     const size_t smem = 7 * (size_t)W * P * es;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;

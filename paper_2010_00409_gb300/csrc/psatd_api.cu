@@ -10,6 +10,10 @@
 
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "../../include/psatd.h"
 #include "common.cuh"
 
@@ -41,12 +45,30 @@ constexpr int kDiagBlocks = 1024;
 
 thread_local std::string g_create_error = "no error";
 
+// autotuner results per (Nx, Ny, Nz, precision): kernel path and tile shift
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
+std::mutex g_tuned_mutex;
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
 };
 
 }  // namespace
+
+struct psatd_batch {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    cudaError_t capture_error = cudaSuccess;
+    std::vector<std::pair<psatd_ctx*, double>> time_advance;   // per replay: ctx time += value
+    std::vector<std::pair<psatd_ctx*, double>> time_set;       // per replay: ctx time = value
+};
+
+namespace {
+thread_local psatd_batch* g_capture = nullptr;   // batch being captured on this thread
+}
 
 struct psatd_ctx {
     psatd_grid grid{};
@@ -73,6 +95,7 @@ struct psatd_ctx {
 
     long long launches = 0;
     int kernel_path = PSATD_PATH_AUTO;
+    int tile_shift = 0;                 // generic-kernel tile width scale (autotuner)
 
     // tensor map of the field storage for the copy-engine-fed k-space kernel
     alignas(64) CUtensorMap field_map;
@@ -148,6 +171,7 @@ GridGeom geom(const psatd_ctx* c) {
 template <typename T>
 Tables<T> tables(const psatd_ctx* c) {
     Tables<T> tb;
+    tb.tile_shift = c->tile_shift;
     for (int a = 0; a < 3; ++a) {
         tb.tw[a] = static_cast<const cplx<T>*>(c->tw[a].p);
         tb.k[a] = static_cast<const T*>(c->k[a].p);
@@ -217,6 +241,8 @@ psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr) {
 psatd_status set_coef(psatd_ctx* c, double dt) {
     return c->prec == 64 ? upload_coef<double>(c, dt) : upload_coef<float>(c, dt);
 }
+
+psatd_batch* capturing(const psatd_ctx* c);
 
 psatd_status check_ctx(psatd_ctx* c, bool need_fields, bool need_physical = false) {
     if (!c) return fail(nullptr, PSATD_ERR_ARG, "NULL context");
@@ -316,6 +342,11 @@ bool ensure_field_map(psatd_ctx* c) {
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     c->field_map_ok = (r == CUDA_SUCCESS);
     return c->field_map_ok;
+}
+
+// The batch capturing this context's stream, if any.
+psatd_batch* capturing(const psatd_ctx* c) {
+    return (g_capture && g_capture->capturing && g_capture->stream == c->stream) ? g_capture : nullptr;
 }
 
 // Read and clear the device error word (synchronises the stream).
@@ -574,6 +605,7 @@ void psatd_destroy(psatd_ctx* c) {
 psatd_status psatd_set_dt(psatd_ctx* c, double dt) {
     psatd_status st = check_ctx(c, false);
     if (st) return st;
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "not allowed while a batch is being captured");
     if (!is_finite(dt)) return fail(c, PSATD_ERR_ARG, "dt must be finite");
     st = set_coef(c, dt);
     if (st == PSATD_OK) c->dt = dt;
@@ -614,6 +646,7 @@ static psatd_status copy_field(psatd_ctx* c, int comp, void* dst, const void* sr
     psatd_status st = check_ctx(c, true);
     if (st) return st;
     if (comp < -1 || comp > 5) return fail(c, PSATD_ERR_ARG, "comp must be -1..5");
+    if (!on_device && capturing(c)) return fail(c, PSATD_ERR_STATE, "host copies are not allowed while a batch is being captured");
     if (!(to_lib ? src : dst)) return fail(c, PSATD_ERR_ARG, "NULL buffer");
     const size_t per = n_cells(c->grid) * cplx_size(c->prec);
     const size_t bytes = comp < 0 ? 6 * per : per;
@@ -696,12 +729,15 @@ psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
     psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (n_steps < 0) return fail(c, PSATD_ERR_ARG, "n_steps must be >= 0");
+    psatd_batch* b = capturing(c);
+    if (b && c->prof_on) return fail(c, PSATD_ERR_STATE, "profiling must be off while capturing a batch");
     for (int s = 0; s < n_steps; ++s) {
         cudaError_t e = c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0)
                                       : spectral_pass<float>(c, KS_ROTATE, 0.0);
         if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
-        c->t += c->dt;
+        if (!b) c->t += c->dt;
     }
+    if (b) b->time_advance.push_back({c, n_steps * c->dt});
     return PSATD_OK;
 }
 
@@ -725,6 +761,7 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
     if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
         return fail(c, PSATD_ERR_ARG, "plane coordinates must be finite");
     if (comp_mask <= 0 || comp_mask > 63) return fail(c, PSATD_ERR_ARG, "comp_mask must select 1..6 components");
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "sample_focal_plane is not captured into batches; use psatd_focal_one_shot");
     int comps[6], nc = 0;
     for (int a = 0; a < 6; ++a)
         if (comp_mask & (1 << a)) comps[nc++] = a;
@@ -770,6 +807,20 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
     if (comp_mask <= 0 || comp_mask > 63) return fail(c, PSATD_ERR_ARG, "comp_mask must select 1..6 components");
     if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
         return fail(c, PSATD_ERR_ARG, "plane coordinates must be finite");
+    psatd_batch* cap = capturing(c);
+    if (cap) {
+        const psatd_grid& g0 = c->grid;
+        int nc0 = 0;
+        for (int a = 0; a < 6; ++a) nc0 += (comp_mask >> a) & 1;
+        const bool ready = c->coef_T_ok && c->coef_T_step == T && dst_on_device && !c->prof_on &&
+                           c->samp_wy.bytes >= (size_t)ny * g0.Ny * sizeof(double2) &&
+                           c->samp_wz.bytes >= (size_t)nz * g0.Nz * sizeof(double2) &&
+                           c->samp_g.bytes >= (size_t)nc0 * g0.Nz * g0.Ny * sizeof(double2) &&
+                           c->samp_h.bytes >= (size_t)nc0 * g0.Nz * ny * sizeof(double2) && c->samp_wx.p;
+        if (!ready)
+            return fail(c, PSATD_ERR_STATE, "inside a batch capture the same one-shot (T, plane size, device "
+                                            "dst) must have run once before, with profiling off");
+    }
     if (!c->coef_T_ok || c->coef_T_step != T) {
         st = c->prec == 64 ? upload_coef<double>(c, T, &c->coef_T) : upload_coef<float>(c, T, &c->coef_T);
         if (st) return st;
@@ -785,6 +836,7 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
     if (e != cudaSuccess) return cuda_fail(c, e, "one-shot launch");
     c->holds_spectrum = true;
     c->t = T;
+    if (cap) cap->time_set.push_back({c, T});
     int comps[6], nc = 0;
     for (int a = 0; a < 6; ++a)
         if (comp_mask & (1 << a)) comps[nc++] = a;
@@ -822,6 +874,7 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
 psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
     psatd_status st = check_ctx(c, true, true);
     if (st) return st;
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "not allowed while a batch is being captured");
     if (!out) return fail(c, PSATD_ERR_ARG, "NULL out");
     const size_t n = n_cells(c->grid);
     const size_t es = cplx_size(c->prec);
@@ -879,6 +932,7 @@ psatd_status psatd_set_time(psatd_ctx* c, double t) {
 psatd_status psatd_synchronize(psatd_ctx* c) {
     psatd_status st = check_ctx(c, false);
     if (st) return st;
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "cannot synchronise while a batch is being captured");
     CK(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c);
 }
@@ -891,6 +945,142 @@ psatd_status psatd_selftest_wait_timeout(psatd_ctx* c) {
     CK(c, launch_wait_timeout_selftest(c->dev_err, c->stream));
     ++c->launches;
     return psatd_synchronize(c);
+}
+
+psatd_status psatd_batch_begin(void* cuda_stream, psatd_batch** out) {
+    if (!out) return fail(nullptr, PSATD_ERR_ARG, "NULL out");
+    *out = nullptr;
+    if (g_capture) return fail(nullptr, PSATD_ERR_STATE, "a batch is already being captured on this thread");
+    psatd_batch* b = new (std::nothrow) psatd_batch();
+    if (!b) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!b->stream) {
+        delete b;
+        return fail(nullptr, PSATD_ERR_ARG, "a batch needs a non-default stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(nullptr, e, "cudaStreamBeginCapture");
+    }
+    b->capturing = true;
+    g_capture = b;
+    *out = b;
+    return PSATD_OK;
+}
+
+psatd_status psatd_batch_end(psatd_batch* b) {
+    if (!b || !b->capturing) return fail(nullptr, PSATD_ERR_ARG, "batch is not capturing");
+    b->capturing = false;
+    g_capture = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGraphInstantiate");
+    return PSATD_OK;
+}
+
+psatd_status psatd_batch_launch(psatd_batch* b) {
+    if (!b || !b->exec) return fail(nullptr, PSATD_ERR_STATE, "batch has no instantiated graph");
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGraphLaunch");
+    for (auto& p : b->time_advance) p.first->t += p.second;
+    for (auto& p : b->time_set) p.first->t = p.second;
+    return PSATD_OK;
+}
+
+long long psatd_batch_nodes(const psatd_batch* b) {
+    if (!b || !b->graph) return 0;
+    size_t n = 0;
+    if (cudaGraphGetNodes(b->graph, nullptr, &n) != cudaSuccess) return 0;
+    return (long long)n;
+}
+
+void psatd_batch_destroy(psatd_batch* b) {
+    if (!b) return;
+    if (b->capturing) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(b->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        if (g_capture == b) g_capture = nullptr;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+psatd_status psatd_autotune(psatd_ctx* c, int trial_steps, int* path_out, int* shift_out, double* ms_out) {
+    psatd_status st = check_ctx(c, true, true);
+    if (st) return st;
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "cannot tune inside a batch capture");
+    if (trial_steps < 1) trial_steps = 2;
+    const auto key = std::make_tuple(c->grid.Nx, c->grid.Ny, c->grid.Nz, c->prec);
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            c->kernel_path = it->second.first;
+            c->tile_shift = it->second.second;
+            if (path_out) *path_out = c->kernel_path;
+            if (shift_out) *shift_out = c->tile_shift;
+            if (ms_out) *ms_out = -1.0;
+            return PSATD_OK;
+        }
+    }
+    // trial runs on a scratch copy so the context's fields stay untouched
+    void* scratch = nullptr;
+    CK(c, cudaMalloc(&scratch, c->field_bytes));
+    void* saved = c->fields;
+    const double t_saved = c->t;
+    const bool prof_saved = c->prof_on;
+    c->prof_on = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best_path = c->kernel_path, best_shift = c->tile_shift;
+    double best_ms = 1e300;
+    cudaError_t err = cudaMemcpyAsync(scratch, saved, c->field_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->fields = scratch;
+    const int paths[3] = {PSATD_PATH_AUTO, PSATD_PATH_REGISTER, PSATD_PATH_GENERIC};
+    for (int pi = 0; pi < 3 && err == cudaSuccess; ++pi) {
+        for (int sh = -1; sh <= 1 && err == cudaSuccess; ++sh) {
+            c->kernel_path = paths[pi];
+            c->tile_shift = sh;
+            for (int w = 0; w < 1 && err == cudaSuccess; ++w)
+                err = c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0) : spectral_pass<float>(c, KS_ROTATE, 0.0);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+            for (int k = 0; k < trial_steps && err == cudaSuccess; ++k)
+                err = c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0) : spectral_pass<float>(c, KS_ROTATE, 0.0);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms / trial_steps < best_ms) {
+                best_ms = ms / trial_steps;
+                best_path = paths[pi];
+                best_shift = sh;
+            }
+        }
+    }
+    c->fields = saved;
+    c->field_map_ptr = nullptr;        // the tensor map was last encoded for the scratch copy
+    c->t = t_saved;
+    c->prof_on = prof_saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(scratch);
+    if (err != cudaSuccess) return cuda_fail(c, err, "autotune trial");
+    c->kernel_path = best_path;
+    c->tile_shift = best_shift;
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mutex);
+        g_tuned[key] = {best_path, best_shift};
+    }
+    if (path_out) *path_out = best_path;
+    if (shift_out) *shift_out = best_shift;
+    if (ms_out) *ms_out = best_ms;
+    return PSATD_OK;
 }
 
 psatd_status psatd_set_kernel_path(psatd_ctx* c, int path) {

@@ -28,7 +28,8 @@ EXPORTS = (
     "psatd_synchronize", "psatd_d_min", "psatd_last_error", "psatd_status_string",
     "psatd_launch_count", "psatd_profile_enable", "psatd_profile_read", "psatd_kernel_name",
     "psatd_set_kernel_path", "psatd_selftest_wait_timeout", "psatd_energy_noalloc",
-    "psatd_focal_one_shot",
+    "psatd_focal_one_shot", "psatd_batch_begin", "psatd_batch_end", "psatd_batch_launch",
+    "psatd_batch_nodes", "psatd_batch_destroy", "psatd_autotune",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -94,6 +95,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_energy_noalloc": (C.c_int, [P, C.c_int, C.c_longlong, C.POINTER(C.c_double), C.c_int, P]),
         "psatd_focal_one_shot": (C.c_int, [P, C.POINTER(PsatdPulse), C.c_double, C.c_double, C.c_int, C.c_int,
                                            C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, P, C.c_int]),
+        "psatd_batch_begin": (C.c_int, [P, C.POINTER(P)]),
+        "psatd_batch_end": (C.c_int, [P]),
+        "psatd_batch_launch": (C.c_int, [P]),
+        "psatd_batch_nodes": (C.c_longlong, [P]),
+        "psatd_batch_destroy": (None, [P]),
+        "psatd_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -135,6 +142,46 @@ def make_grid(g) -> PsatdGrid:
 def make_pulse(p) -> PsatdPulse:
     return PsatdPulse(p.kind, p.div_project, p.lam, p.theta, p.eps, p.P0, p.n_cycles, p.cep,
                       p.ellipticity, p.pol_angle)
+
+
+class Batch:
+    """A CUDA graph of library calls recorded on one stream (see psatd_batch_*).
+
+        with Batch(stream) as b:        # records
+            ctx1.advance(4); ctx2.focal_one_shot(..., out=dev_tensor)
+        b.launch()                      # replays with one graph launch
+    """
+
+    def __init__(self, stream):
+        self.stream = stream
+        self._ptr = C.c_void_p()
+
+    def __enter__(self):
+        _check(lib().psatd_batch_begin(C.c_void_p(self.stream.cuda_stream), C.byref(self._ptr)), None)
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        st = lib().psatd_batch_end(self._ptr)
+        if exc_type is None:
+            _check(st, None)
+
+    def launch(self):
+        _check(lib().psatd_batch_launch(self._ptr), None)
+
+    @property
+    def nodes(self) -> int:
+        return lib().psatd_batch_nodes(self._ptr)
+
+    def close(self):
+        if self._ptr and self._ptr.value:
+            lib().psatd_batch_destroy(self._ptr)
+            self._ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:
@@ -265,6 +312,11 @@ class Context:
     @property
     def launch_count(self) -> int:
         return lib().psatd_launch_count(self._ptr)
+
+    def autotune(self, trial_steps: int = 2):
+        path, shift, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().psatd_autotune(self._ptr, trial_steps, C.byref(path), C.byref(shift), C.byref(ms)), self._ptr)
+        return path.value, shift.value, ms.value
 
     def set_kernel_path(self, path: int):
         _check(lib().psatd_set_kernel_path(self._ptr, path), self._ptr)

@@ -173,3 +173,52 @@ def plane_points(plane: dict):
     ys = plane["y0"] + (plane["y1"] - plane["y0"]) * np.arange(plane["ny"]) / plane["ny"]
     zs = plane["z0"] + (plane["z1"] - plane["z0"]) * np.arange(plane["nz"]) / plane["nz"]
     return ys, zs
+
+
+# --------------------------------------------------------------------------
+# Batched sweep: seeded pulse realisations on uneven mapped grids
+# --------------------------------------------------------------------------
+SWEEP_SIZES = (96, 100, 108, 120, 128, 135, 144, 150, 160, 162, 180, 192)
+
+
+def _sweep_size(n_needed: int) -> int:
+    for n in SWEEP_SIZES:
+        if n >= n_needed:
+            return n
+    return SWEEP_SIZES[-1]
+
+
+def batched_sweep(n: int = 64, seed: int = 0, lam: float = LAMBDA0):
+    """n seeded 2-cycle Gaussian realisations: f-number ~ U[0.5, 2], CEP ~
+    U[0, 2 pi), ellipticity ~ U[0, 1], R0 = max(20, 10 f^2) lam, L = 9 lam.
+
+    Each gets its own periodic layer: D is 5 % above the x-extent of the shell
+    sector (R_max - R_min cos(support angle)), so replicas never overlap; the
+    transverse half-width is R_max sin(support) + lam.  Grid sizes are the
+    smallest of SWEEP_SIZES reaching 8 points per wavelength along x and, across,
+    a step 30 % below the Nyquist limit lam / (2 sin(support)) of the pulse's
+    largest transverse wavenumber (capped at 192).  Returns a list of
+    (grid, mapping, pulse, T, plane) with T = R0/c and a 64 x 64 focal plane.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        f = rng.uniform(0.5, 2.0)
+        cep = rng.uniform(0.0, 2 * np.pi)
+        ell = rng.uniform(0.0, 1.0)
+        theta0 = math.atan(1.0 / (2.0 * f))
+        R0 = max(20.0, 10.0 * f * f) * lam
+        L = 9.0 * lam
+        support = 2 * theta0 + 0.1
+        r_min, r_max = R0 - L / 2, R0 + L / 2
+        D = 1.05 * (r_max - r_min * math.cos(support))
+        Nx = _sweep_size(math.ceil(D / (lam / 8)))
+        s_max = math.sin(min(support, math.pi / 2))
+        H = r_max * s_max + lam
+        Nt = _sweep_size(math.ceil(2 * H / (lam / (2.6 * s_max))))
+        g = GridSpec(Nx, Nt, Nt, D / Nx, 2 * H / Nt, 2 * H / Nt, -r_min - D, -H, -H, C_CGS)
+        p = PulseSpec(kind=GAUSSIAN, lam=lam, theta=theta0, eps=0.2, P0=1e7, n_cycles=2.0, cep=cep,
+                      ellipticity=ell, pol_angle=0.0, div_project=1)
+        plane = dict(x_p=0.0, ny=64, nz=64, y0=-1.5 * lam, y1=1.5 * lam, z0=-1.5 * lam, z1=1.5 * lam)
+        out.append((g, MappingSpec(R0, L), p, R0 / C_CGS, plane))
+    return out
