@@ -118,6 +118,10 @@ void psatd_destroy(psatd_ctx* ctx);
  * vacuum solver is exact in time for any step). */
 psatd_status psatd_set_dt(psatd_ctx* ctx, double dt);
 
+/* Replace the shell geometry used by later psatd_init_pulse,
+ * psatd_focal_one_shot and psatd_sample_focal_plane calls. */
+psatd_status psatd_set_mapping(psatd_ctx* ctx, const psatd_mapping* mapping);
+
 /* Use caller-owned device memory (e.g. a torch tensor) as the field storage.
  * bytes must be at least 6*Nx*Ny*Nz*(8 or 16) and dev_ptr 256-byte aligned.
  * Library-owned storage, if any, is freed.  The memory must outlive the context
@@ -148,7 +152,10 @@ psatd_status psatd_advance(psatd_ctx* ctx, int n_steps);
  * unnormalised.  Asynchronous. */
 psatd_status psatd_fft(psatd_ctx* ctx, int direction);
 
-/* Sample the physical field on the plane x = x_phys at y_p = y0 + p (y1-y0)/ny,
+/* After psatd_focal_one_shot (storage holds the updated spectrum) this samples
+ * the same interpolant from the spectrum, so further planes of the focal region
+ * cost no transform.
+ * Sample the physical field on the plane x = x_phys at y_p = y0 + p (y1-y0)/ny,
  * z_q = z0 + q (z1-z0)/nz (p < ny, q < nz) at the current time t, as
  * u(R, t) = u~(T(R)) I_S(t)(R) (Eq. 13-16) with u~ the exact trigonometric
  * interpolant of the grid field.  comp_mask selects components (bit c = component
@@ -165,8 +172,9 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* ctx, double x_phys, int ny, int
  * and sample the plane x = x_phys at time T exactly as psatd_sample_focal_plane,
  * evaluating the interpolant straight from the updated spectrum (no inverse 3D
  * transform).  Afterwards the field storage holds that spectrum, so advance,
- * fft, diagnostics and sample_focal_plane return PSATD_ERR_STATE until a pulse
- * or all six components are set again; psatd_time() is T.  The coefficient
+ * fft and diagnostics return PSATD_ERR_STATE until a pulse
+ * or all six components are set again (psatd_sample_focal_plane keeps working,
+ * from the spectrum); psatd_time() is T.  The coefficient
  * table for T is built on the host (float64) and cached for the next call with
  * the same T. */
 psatd_status psatd_focal_one_shot(psatd_ctx* ctx, const psatd_pulse* pulse, double T, double x_phys,
@@ -255,6 +263,55 @@ void psatd_batch_destroy(psatd_batch* batch);
  * precision for the process (later calls for the same shape apply the cached
  * choice without timing and report ms_per_step = -1).  Outputs may be NULL. */
 psatd_status psatd_autotune(psatd_ctx* ctx, int trial_steps, int* path, int* tile_shift, double* ms_per_step);
+
+/* ---------------------------------------------------------------------------
+ * Surrogate: a Fourier neural operator from pulse parameters to the field on a
+ * focal patch, trained and evaluated with the library's own kernels (tensor-core
+ * GEMMs in bfloat16 with float32 accumulation, float32 elsewhere).  The paper
+ * has no counterpart; it motivates statistical sweeps (Sec. 3.2.3) whose focal
+ * fields the solver produces and judges.
+ *   v0 = W_lift [p_1..p_n, x, y, z] + b,  v_l = act(S_l v_{l-1} + W_l v_{l-1} + b_l)
+ *   out = W_q2 GELU(W_q1 v_L + b_q1) + b_q2
+ * S_l: truncated DFT (kx in [0, modes), ky, kz in {0..modes-1, P-modes..P-1}),
+ * a complex width x width matrix per kept mode, inverse DFT; act = GELU except
+ * on the last layer.  Coordinates are -1 + 2 i / patch.  Tensors are float32,
+ * sample-major: params [batch][in_params], output and targets
+ * [batch][out_channels][patch^3] with x fastest. */
+typedef struct psatd_fno psatd_fno;
+typedef struct psatd_fno_config {
+    int in_params;      /* scalar inputs per sample (coordinates are added) */
+    int width;          /* channels */
+    int layers;         /* spectral layers */
+    int patch;          /* P: output patch P^3, even, 4..128 */
+    int modes;          /* kept modes per sign and axis, 2*modes <= P */
+    int hidden;         /* projection hidden channels */
+    int out_channels;
+    int max_batch;
+} psatd_fno_config;
+/* Allocate parameters (seeded uniform initialisation), Adam state and the
+ * activation buffers for max_batch samples on the current device. */
+psatd_status psatd_fno_create(const psatd_fno_config* cfg, unsigned long long seed, void* cuda_stream,
+                              psatd_fno** out);
+void psatd_fno_destroy(psatd_fno* fno);
+long long psatd_fno_num_params(const psatd_fno* fno);
+/* Device pointers of the flat parameter vector, its gradient and the last
+ * forward output (owned by the model). */
+psatd_status psatd_fno_buffers(psatd_fno* fno, float** params, float** grads, float** output);
+/* Forward pass; out may be NULL (the result stays in the model's output buffer). */
+psatd_status psatd_fno_forward(psatd_fno* fno, const float* params_dev, int batch, float* out_dev);
+/* Forward, mean squared error against target, backward: gradients overwrite the
+ * gradient vector; *loss (may be NULL) is set after a synchronisation. */
+psatd_status psatd_fno_loss_backward(psatd_fno* fno, const float* params_dev, int batch, const float* target_dev,
+                                     double* loss);
+psatd_status psatd_fno_adam_step(psatd_fno* fno, float lr, float beta1, float beta2, float eps, float weight_decay);
+psatd_status psatd_fno_synchronize(psatd_fno* fno);
+const char* psatd_fno_last_error(const psatd_fno* fno);
+
+/* The tensor-core GEMM used by the surrogate, on device float32 matrices with
+ * arbitrary strides: C = alpha A B + beta C (A: M x K, B: K x N). */
+psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm, long long sAk, const float* B,
+                             long long sBk, long long sBn, float* C, long long sCm, long long sCn, float alpha,
+                             float beta, int ksplit, void* cuda_stream);
 
 /* Kernel kinds for per-kernel timing. */
 enum {

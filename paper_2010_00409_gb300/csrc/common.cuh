@@ -160,4 +160,22 @@ cudaError_t launch_divergence(const cplx<T>* spec3, const GridGeom& g, const Tab
 cudaError_t launch_reduce_final(const double* partial, int nblocks, int width, int nsum,
                                 double* out, cudaStream_t s, long long* nlaunch);
 
+// Strided batched GEMM on the tensor cores (gemm.cu): C[b] = alpha A[b] B[b] +
+// beta C[b], A[b](m,k) = A[b0 sAb0 + b1 sAb1 + m sAm + k sAk], b = (b0, b1), float32
+// in memory, bfloat16 tiles, float32 accumulation; ksplit > 1 splits K over
+// blocks with float atomics.
+struct GemmArgs {
+    int M, N, K;
+    int nb0, nb1;                 // batch = nb0 x nb1
+    const float* A;
+    long long sAb0, sAb1, sAm, sAk;
+    const float* B;
+    long long sBb0, sBb1, sBk, sBn;
+    float* C;
+    long long sCb0, sCb1, sCm, sCn;
+    float alpha, beta;
+    int ksplit;
+};
+cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s);
+
 }  // namespace psatd

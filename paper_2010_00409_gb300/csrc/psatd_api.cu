@@ -612,6 +612,13 @@ psatd_status psatd_set_dt(psatd_ctx* c, double dt) {
     return st;
 }
 
+psatd_status psatd_set_mapping(psatd_ctx* c, const psatd_mapping* m) {
+    if (!c || !m) return fail(c, PSATD_ERR_ARG, "NULL argument");
+    if (!(is_finite(m->R0) && is_finite(m->L) && m->L >= 0)) return fail(c, PSATD_ERR_ARG, "mapping R0, L must be finite, L >= 0");
+    c->mapping = *m;
+    return PSATD_OK;
+}
+
 psatd_status psatd_bind_fields(psatd_ctx* c, void* dev_ptr, size_t bytes) {
     psatd_status st = check_ctx(c, false);
     if (st) return st;
@@ -754,7 +761,7 @@ psatd_status psatd_fft(psatd_ctx* c, int direction) {
 
 psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int nz, double y0, double y1,
                                       double z0, double z1, int comp_mask, void* dst, int dst_on_device) {
-    psatd_status st = check_ctx(c, true, true);
+    psatd_status st = check_ctx(c, true);
     if (st) return st;
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
@@ -784,8 +791,8 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
     const GridGeom gg = geom(c);
     cudaError_t e = timed(c, PSATD_KERNEL_SAMPLE, [&] {
         return c->prec == 64
-            ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches)
-            : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches);
+            ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches, c->holds_spectrum)
+            : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches, c->holds_spectrum);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "sample launch");
     if (!dst_on_device) {

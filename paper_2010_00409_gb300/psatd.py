@@ -30,6 +30,9 @@ EXPORTS = (
     "psatd_set_kernel_path", "psatd_selftest_wait_timeout", "psatd_energy_noalloc",
     "psatd_focal_one_shot", "psatd_batch_begin", "psatd_batch_end", "psatd_batch_launch",
     "psatd_batch_nodes", "psatd_batch_destroy", "psatd_autotune",
+    "psatd_fno_create", "psatd_fno_destroy", "psatd_fno_num_params", "psatd_fno_buffers", "psatd_fno_forward",
+    "psatd_fno_loss_backward", "psatd_fno_adam_step", "psatd_fno_synchronize", "psatd_fno_last_error",
+    "psatd_gemm_bf16", "psatd_set_mapping",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -53,6 +56,11 @@ class PsatdPulse(C.Structure):
                 ("lambda_", C.c_double), ("theta", C.c_double), ("eps", C.c_double),
                 ("P0", C.c_double), ("n_cycles", C.c_double), ("cep", C.c_double),
                 ("ellipticity", C.c_double), ("pol_angle", C.c_double)]
+
+
+class PsatdFnoConfig(C.Structure):
+    _fields_ = [("in_params", C.c_int), ("width", C.c_int), ("layers", C.c_int), ("patch", C.c_int),
+                ("modes", C.c_int), ("hidden", C.c_int), ("out_channels", C.c_int), ("max_batch", C.c_int)]
 
 
 class PsatdDiag(C.Structure):
@@ -101,6 +109,18 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_batch_nodes": (C.c_longlong, [P]),
         "psatd_batch_destroy": (None, [P]),
         "psatd_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "psatd_fno_create": (C.c_int, [C.POINTER(PsatdFnoConfig), C.c_ulonglong, P, C.POINTER(P)]),
+        "psatd_fno_destroy": (None, [P]),
+        "psatd_fno_num_params": (C.c_longlong, [P]),
+        "psatd_fno_buffers": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
+        "psatd_fno_forward": (C.c_int, [P, P, C.c_int, P]),
+        "psatd_fno_loss_backward": (C.c_int, [P, P, C.c_int, P, C.POINTER(C.c_double)]),
+        "psatd_fno_adam_step": (C.c_int, [P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "psatd_fno_synchronize": (C.c_int, [P]),
+        "psatd_fno_last_error": (C.c_char_p, [P]),
+        "psatd_set_mapping": (C.c_int, [P, C.POINTER(PsatdMapping)]),
+        "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
+                                      C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +204,100 @@ class Batch:
             pass
 
 
+class Fno:
+    """The surrogate network (psatd_fno_*): parameters, gradients and output are
+    device tensors owned by the model and exposed as torch views."""
+
+    def __init__(self, in_params, width=32, layers=4, patch=64, modes=12, hidden=64, out_channels=3,
+                 max_batch=8, seed=0, stream=None):
+        import torch
+        self._torch = torch
+        self.cfg = PsatdFnoConfig(in_params, width, layers, patch, modes, hidden, out_channels, max_batch)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._ptr = C.c_void_p()
+        st = lib().psatd_fno_create(C.byref(self.cfg), seed, C.c_void_p(self.stream.cuda_stream), C.byref(self._ptr))
+        if st != OK:
+            raise PsatdError(st, "psatd_fno_create failed")
+        self.n_params = lib().psatd_fno_num_params(self._ptr)
+        pp, gp, op = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        lib().psatd_fno_buffers(self._ptr, C.byref(pp), C.byref(gp), C.byref(op))
+        self._bufs = (pp.value, gp.value, op.value)
+        self.device = dev
+
+    @property
+    def params(self):
+        return _device_view(self._bufs[0], self.n_params, self.device)
+
+    @property
+    def grads(self):
+        return _device_view(self._bufs[1], self.n_params, self.device)
+
+    def output(self, batch):
+        c = self.cfg
+        return _device_view(self._bufs[2], batch * c.out_channels * c.patch ** 3, self.device).view(
+            batch, c.out_channels, c.patch, c.patch, c.patch)
+
+    def _check(self, st):
+        if st != OK:
+            raise PsatdError(st, lib().psatd_fno_last_error(self._ptr).decode())
+
+    def forward(self, prm):
+        """prm: float32 CUDA tensor [B][in_params]; returns the output view."""
+        B = prm.shape[0]
+        self._check(lib().psatd_fno_forward(self._ptr, C.c_void_p(prm.data_ptr()), B, None))
+        return self.output(B)
+
+    def loss_backward(self, prm, target, want_loss=True):
+        loss = C.c_double()
+        self._check(lib().psatd_fno_loss_backward(self._ptr, C.c_void_p(prm.data_ptr()), prm.shape[0],
+                                                  C.c_void_p(target.data_ptr()), C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        self._check(lib().psatd_fno_adam_step(self._ptr, lr, beta1, beta2, eps, weight_decay))
+
+    def synchronize(self):
+        self._check(lib().psatd_fno_synchronize(self._ptr))
+
+    def close(self):
+        if self._ptr and self._ptr.value:
+            lib().psatd_fno_destroy(self._ptr)
+            self._ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(addr, n, device):
+    """A float32 torch tensor aliasing n floats of device memory at addr (the
+    owner keeps the memory alive)."""
+    import torch
+
+    class _Holder:
+        def __init__(self, ptr, size):
+            self.__cuda_array_interface__ = {"shape": (size,), "typestr": "<f4", "data": (ptr, False),
+                                             "version": 2, "strides": None}
+    return torch.as_tensor(_Holder(addr, n), device=device)
+
+
+def gemm_bf16(A, B, Cout, alpha=1.0, beta=0.0, ksplit=1, stream=None):
+    """Cout = alpha A B + beta Cout on float32 CUDA tensors (2-D, any strides)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2 and tuple(Cout.shape) == (M, N)
+    st = lib().psatd_gemm_bf16(M, N, K, C.c_void_p(A.data_ptr()), A.stride(0), A.stride(1), C.c_void_p(B.data_ptr()),
+                               B.stride(0), B.stride(1), C.c_void_p(Cout.data_ptr()), Cout.stride(0), Cout.stride(1),
+                               alpha, beta, ksplit, C.c_void_p(s.cuda_stream))
+    _check(st, None)
+    return Cout
+
+
 class Context:
     """One periodic box on the current CUDA device; fields are a torch tensor
     [6, Nz, Ny, Nx] (complex64 or complex128) bound to the library."""
@@ -230,6 +344,10 @@ class Context:
         self.close()
 
     # -- calls
+    def set_mapping(self, mapping):
+        m = PsatdMapping(mapping.R0, mapping.L)
+        _check(lib().psatd_set_mapping(self._ptr, C.byref(m)), self._ptr)
+
     def set_dt(self, dt: float):
         _check(lib().psatd_set_dt(self._ptr, dt), self._ptr)
 

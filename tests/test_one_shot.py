@@ -38,6 +38,9 @@ def test_one_shot_matches_oracle(lib, prec, N, project, path):
         assert abs(ctx.time - T) == 0.0
         with pytest.raises(lib.PsatdError):
             ctx.advance(1)                         # storage holds the spectrum now
+        again = ctx.sample_focal_plane(plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"],
+                                       plane["z0"], plane["z1"], comps=(0, 1, 2))
+        assert np.array_equal(again, got)          # sampled from the held spectrum
         ctx.init_pulse(p)
         ctx.advance(0)
     og, om = ogrid(g), O.Mapping(m.R0, m.L)
