@@ -57,6 +57,12 @@ def dist_env():
     return RP.env()
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu capture of the default command at 256^3 (mean of
+# the forward and inverse launches); to be re-taken whenever that kernel changes.
+NCU_TRAFFIC_BYTES = {("plane_xy", 256): 1549.95e6}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -245,7 +251,7 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_src == "measured" else "fallback 6.8 TB/s",
-                     "traffic": None, "bytes_per_launch": bytes_per_launch,
+                     "traffic": NCU_TRAFFIC_BYTES.get((dom, a.size)), "bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": dom_ms / dom_n, "launches": dom_n},
         "kernel_share": {k: round(v[0] / all_total, 4) for k, v in sorted(prof.items())},
         "step_hbm": {"algorithmic_bytes_per_cell_step": sweep_bytes / (g.cells * n_steps * a.steps),
