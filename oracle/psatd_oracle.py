@@ -29,6 +29,11 @@ design notes):
   R12 Gaussian pulse: u_ts = exp(-a^2/t0^2) times the Eq. 5 edge with
       theta = 2*t0; u_l windowed to |zeta| <= L/2; CGS amplitude.
   R13 CEP phi, ellipticity e and polarisation angle psi.
+  R20 real fields: one step of real E, B is the real part of the complex
+      step.  Eq. 3-4 keep a Hermitian spectrum Hermitian except on Nyquist
+      planes, where the wave number -pi/d is its own mirror index; the real
+      part there is the mean of the update at kappa and at kappa with its
+      Nyquist components negated.
 """
 from __future__ import annotations
 
@@ -41,6 +46,7 @@ __all__ = [
     "Grid", "Mapping", "Pulse", "FLAT_TOP", "GAUSSIAN",
     "wavenumbers", "fft3", "ifft3", "dft3_naive", "idft3_naive",
     "psatd_update", "psatd_step", "advance", "advance_exact",
+    "psatd_step_real", "advance_real",
     "theta_from_fnumber", "d_min", "mapping_T", "indicator_S",
     "omega", "u_ts_flat", "u_l_flat", "flat_top_A", "F_series", "F_exact",
     "gaussian_E0", "pulse_scalar", "polarisation_vectors",
@@ -220,6 +226,20 @@ def advance_exact(fields: np.ndarray, grid: Grid, T: float) -> np.ndarray:
     """A single step of size T.  In vacuum the solver is exact in time, so this
     equals any number of steps summing to T up to rounding (Sec. 2.1, Sec. 3.1)."""
     return psatd_step(np.asarray(fields, dtype=np.complex128), grid, T)
+
+
+def psatd_step_real(fields: np.ndarray, grid: Grid, dt: float) -> np.ndarray:
+    """One step of real fields [6, Nz, Ny, Nx] (float64): the real part of the
+    complex step of Sec. 2.1 applied to them (R20)."""
+    return psatd_step(np.asarray(fields, dtype=np.float64).astype(np.complex128), grid, dt).real
+
+
+def advance_real(fields: np.ndarray, grid: Grid, dt: float, n: int) -> np.ndarray:
+    """n consecutive real-field steps of size dt (R20)."""
+    f = np.array(fields, dtype=np.float64, copy=True)
+    for _ in range(n):
+        f = psatd_step_real(f, grid, dt)
+    return f
 
 
 def courant_dt(grid: Grid) -> float:

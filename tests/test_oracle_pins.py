@@ -454,3 +454,82 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     for bad in (flipped_i, no_projection, swapped_components, sin_for_cos):
         assert not _pins_pass(monkeypatch, bad), bad.__name__
     monkeypatch.setattr(O, "psatd_update", good)
+
+
+# ------------------------------------------------------------ real fields (R20)
+def _real_field(grid, seed, nyquist=True):
+    """Random real fields; with nyquist=False every Nyquist plane of the
+    spectrum is zeroed (the field stays real: those planes are self-mirrored)."""
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((6, grid.Nz, grid.Ny, grid.Nx))
+    if not nyquist:
+        F = np.fft.fftn(f, axes=(1, 2, 3))
+        for ax, N in ((3, grid.Nx), (2, grid.Ny), (1, grid.Nz)):
+            if N % 2 == 0:
+                idx = [slice(None)] * 4
+                idx[ax] = N // 2
+                F[tuple(idx)] = 0
+        f = np.fft.ifftn(F, axes=(1, 2, 3))
+        assert np.max(np.abs(f.imag)) < 1e-12
+        f = f.real
+    return f
+
+
+def test_complex_step_keeps_band_limited_real_fields_real():
+    g = small_grid(8, 6, 10)
+    f = _real_field(g, 3, nyquist=False)
+    out = O.psatd_step(f.astype(np.complex128), g, 0.37)
+    assert np.max(np.abs(out.imag)) <= 1e-13 * np.max(np.abs(out.real))
+    assert np.allclose(O.psatd_step_real(f, g, 0.37), out.real, rtol=0, atol=1e-14 * np.max(np.abs(f)))
+
+
+def _rotate_one_mode(E, B, kvec, c, dt):
+    """Eq. 3-4 for one mode, written with vector products."""
+    kn = float(np.linalg.norm(kvec))
+    if kn == 0.0:
+        return E.copy(), B.copy()
+    n = kvec / kn
+    C, S = math.cos(c * kn * dt), math.sin(c * kn * dt)
+    return C * (E - n * np.dot(n, E)) + 1j * S * np.cross(n, B), C * B - 1j * S * np.cross(n, E)
+
+
+def test_real_step_is_mean_update_at_mirrored_nyquist_wavevectors():
+    # brute force over every mode of a grid with Nyquist planes on all axes
+    g = small_grid(4, 4, 6)
+    dt = 0.41
+    f = _real_field(g, 5, nyquist=True)
+    Fk = np.fft.fftn(f, axes=(1, 2, 3))
+    kx, ky, kz = (O.wavenumbers(g.Nx, g.dx), O.wavenumbers(g.Ny, g.dy), O.wavenumbers(g.Nz, g.dz))
+    out = np.zeros_like(Fk)
+    for iz in range(g.Nz):
+        for iy in range(g.Ny):
+            for ix in range(g.Nx):
+                kap = np.array([kx[ix], ky[iy], kz[iz]])
+                flip = np.array([ix == g.Nx // 2, iy == g.Ny // 2, iz == g.Nz // 2])
+                kap2 = np.where(flip, -kap, kap)
+                E, B = Fk[0:3, iz, iy, ix], Fk[3:6, iz, iy, ix]
+                E1, B1 = _rotate_one_mode(E, B, kap, g.c, dt)
+                E2, B2 = _rotate_one_mode(E, B, kap2, g.c, dt)
+                out[0:3, iz, iy, ix] = 0.5 * (E1 + E2)
+                out[3:6, iz, iy, ix] = 0.5 * (B1 + B2)
+    want = np.fft.ifftn(out, axes=(1, 2, 3))
+    assert np.max(np.abs(want.imag)) <= 1e-13 * np.max(np.abs(want.real))
+    got = O.psatd_step_real(f, g, dt)
+    assert np.max(np.abs(got - want.real)) <= 1e-13 * np.max(np.abs(want.real))
+    # the Nyquist planes matter here: the plain update leaves an imaginary part
+    assert np.max(np.abs(O.psatd_step(f.astype(np.complex128), g, dt).imag)) > 1e-3 * np.max(np.abs(f))
+
+
+def test_real_step_does_not_increase_energy():
+    g = small_grid(8, 6, 10)
+    f = _real_field(g, 7, nyquist=True)
+    e0 = np.sum(f * f)
+    f1 = O.advance_real(f, g, 0.29, 5)
+    assert np.sum(f1 * f1) <= e0 * (1 + 1e-13)
+    # transverse band-limited fields keep their energy (Parseval, Eq. 3-4 unitary)
+    fb = O.project_transverse(_real_field(g, 7, nyquist=False).astype(np.complex128), g)
+    assert np.max(np.abs(fb.imag)) <= 1e-13 * np.max(np.abs(fb.real))
+    fb = fb.real
+    eb = np.sum(fb * fb)
+    fb1 = O.advance_real(fb, g, 0.29, 5)
+    assert abs(np.sum(fb1 * fb1) / eb - 1) <= 1e-13
