@@ -50,7 +50,8 @@ typedef enum psatd_status {
 
 enum { PSATD_PULSE_FLAT_TOP = 0, PSATD_PULSE_GAUSSIAN = 1 };
 enum { PSATD_FORWARD = -1, PSATD_INVERSE = +1 };
-enum { PSATD_FLAG_NO_FIELD_ALLOC = 1 };   /* init_grid: caller binds field storage */
+enum { PSATD_FLAG_NO_FIELD_ALLOC = 1,     /* init_grid: caller binds field storage */
+       PSATD_FLAG_REAL_FIELDS = 2 };     /* init_grid: real field storage (see below) */
 
 /* The periodic box (Sec. 2.3): D = Nx*dx is the period of the mapped layer. */
 typedef struct psatd_grid {
@@ -105,6 +106,18 @@ typedef struct psatd_diag {
  * dt is the step of psatd_advance; precision is 32 or 64; cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  The mapping geometry is only
  * needed by psatd_init_pulse and psatd_sample_focal_plane.
+ *
+ * Field storage is complex [6][Nz][Ny][Nx] (8 or 16 bytes per value) by
+ * default.  With PSATD_FLAG_REAL_FIELDS it is real float32 [6][Nz][Ny][Nx]
+ * (4 bytes per value; the physical E and B are real): precision must be 32,
+ * Nx = Ny = 256 and Nz one of 64, 128, 256 (else PSATD_ERR_ARG).  A real-field
+ * step is the real part of the complex step (Sec. 2.1, Eq. 3-4; on Nyquist
+ * planes this is the mean of the update at the two mirrored wave vectors) and
+ * moves half the bytes.  In that mode psatd_fft and psatd_focal_one_shot
+ * return PSATD_ERR_STATE (psatd_energy_noalloc reads complex storage only),
+ * psatd_autotune keeps the one real-field kernel set; psatd_init_pulse,
+ * psatd_sample_focal_plane and psatd_diagnostics work through a complex scratch
+ * copy that the context allocates on first use (48 bytes per cell).
  * Cites: Sec. 2.1 (solver), Sec. 2.3 (periodic layer). */
 psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mapping,
                              double dt, int precision, void* cuda_stream, int flags,
@@ -123,7 +136,8 @@ psatd_status psatd_set_dt(psatd_ctx* ctx, double dt);
 psatd_status psatd_set_mapping(psatd_ctx* ctx, const psatd_mapping* mapping);
 
 /* Use caller-owned device memory (e.g. a torch tensor) as the field storage.
- * bytes must be at least 6*Nx*Ny*Nz*(8 or 16) and dev_ptr 256-byte aligned.
+ * bytes must be at least 6*Nx*Ny*Nz*(8 or 16; 4 with real fields) and dev_ptr
+ * 256-byte aligned.
  * Library-owned storage, if any, is freed.  The memory must outlive the context
  * or the next bind. */
 psatd_status psatd_bind_fields(psatd_ctx* ctx, void* dev_ptr, size_t bytes);
@@ -322,8 +336,9 @@ enum {
     PSATD_KERNEL_INIT = 4,       /* pulse initialisation */
     PSATD_KERNEL_SAMPLE = 5,     /* focal-plane sampling (all of its launches) */
     PSATD_KERNEL_DIAG = 6,       /* energy / divergence reductions */
-    PSATD_KERNEL_PLANE_XY = 7,   /* fused x+y plane FFT */
-    PSATD_KERNEL_KINDS = 8
+    PSATD_KERNEL_PLANE_XY = 7,   /* fused x+y plane FFT (real fields: r2c / c2r plane kernels) */
+    PSATD_KERNEL_KSPACE_X0 = 8,  /* real fields: the packed k_x = 0 / Nyquist slot */
+    PSATD_KERNEL_KINDS = 9
 };
 
 /* Start (enable != 0) or stop per-kernel timing: while enabled every launch of

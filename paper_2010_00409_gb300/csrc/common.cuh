@@ -104,13 +104,39 @@ cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, co
 template <typename T>
 cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
 
+// Half spectrum of real fields in the slot order of the real-field plane
+// kernels: per slot p < Nx/2, the wave number k_x and the octant index |m_x|.
+template <typename T> struct HalfSlots {
+    const T* k;
+    const int* ax;
+};
+
 // Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
-// 8-byte elements {Nx * sizeof(complex)/8, Ny, Nz, 6} with box
-// {kspace_tma_box_x(prec), 1, kspace_tma_box_z(Nz), 1}.  Device errors are OR-ed
-// into *err.
+// 8-byte elements {nx * sizeof(complex)/8, Ny, Nz, 6} (nx = Nx, or Nx/2 slots
+// for the half spectrum) with box {kspace_tma_box_x(prec), 1,
+// kspace_tma_box_z(Nz), 1}.  Device errors are OR-ed into *err.  With `half`
+// the storage is a real-field half spectrum (rotation only; slot 0 untouched).
 template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s, bool spectral_out = false, bool project_b = false);
+                              int* err, cudaStream_t s, bool spectral_out = false, bool project_b = false,
+                              const HalfSlots<T>* half = nullptr);
+
+// Slot 0 of a real-field half spectrum (k_x = 0 packed with the x Nyquist
+// mode): unpack the two Hermitian spectra, apply the update, repack; all six
+// components, z transforms included.
+cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float>& tb, cudaStream_t s);
+
+// Real-field plane transforms (FP32, 256 x 256 planes, in place): dir < 0 =
+// r2c along x + y, dir > 0 = inverse y + c2r.  Spectra are in slot order
+// (plane_rc_slot_mode(p) = x mode index of slot p).
+cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
+                            cudaStream_t s);
+bool plane_rc_supported(int prec, const GridGeom& g);
+int plane_rc_slot_mode(int p);
+
+// Real <-> complex copies of n values (widen: im = 0; narrow: keep re).
+cudaError_t launch_widen(const float* in, float2* out, size_t n, cudaStream_t s);
+cudaError_t launch_narrow(const float2* in, float* out, size_t n, cudaStream_t s);
 int kspace_tma_box_x(int prec);
 int kspace_tma_box_z(int Nz);
 cudaError_t launch_wait_timeout_selftest(int* err, cudaStream_t s);

@@ -318,4 +318,41 @@ __device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& E
     Ex = nEx; Ey = nEy; Ez = nEz;
 }
 
+// Real fields: on a Nyquist plane the wave number -pi/d is its own mirror, so the
+// update that keeps the field real is the mean of the update at n and at m = n
+// with the Nyquist components (flags fx, fy, fz) negated:
+//   E <- C'(E - (n(n.E) + m(m.E))/2) + i S' a x B,  B <- C' B - i S' a x E,
+// with a = (n + m)/2 (the Nyquist components of n removed).  Off the Nyquist
+// planes m = n and this is rotate_mode.
+template <typename T>
+__device__ __forceinline__ void rotate_mode_mean(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& Ez, cplx<T>& Bx,
+                                                 cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, bool fx, bool fy,
+                                                 bool fz, T C, T S) {
+    if (!(fx || fy || fz)) {
+        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, nx, ny, nz, C, S);
+        return;
+    }
+    const T mx = fx ? -nx : nx, my = fy ? -ny : ny, mz = fz ? -nz : nz;
+    const T ax = fx ? T(0) : nx, ay = fy ? T(0) : ny, az = fz ? T(0) : nz;
+    const T nEr = nx * Ex.x + ny * Ey.x + nz * Ez.x, nEi = nx * Ex.y + ny * Ey.y + nz * Ez.y;
+    const T mEr = mx * Ex.x + my * Ey.x + mz * Ez.x, mEi = mx * Ex.y + my * Ey.y + mz * Ez.y;
+    const T h = T(0.5);
+    const T cBxr = ay * Bz.x - az * By.x, cBxi = ay * Bz.y - az * By.y;
+    const T cByr = az * Bx.x - ax * Bz.x, cByi = az * Bx.y - ax * Bz.y;
+    const T cBzr = ax * By.x - ay * Bx.x, cBzi = ax * By.y - ay * Bx.y;
+    const T cExr = ay * Ez.x - az * Ey.x, cExi = ay * Ez.y - az * Ey.y;
+    const T cEyr = az * Ex.x - ax * Ez.x, cEyi = az * Ex.y - ax * Ez.y;
+    const T cEzr = ax * Ey.x - ay * Ex.x, cEzi = ax * Ey.y - ay * Ex.y;
+    const cplx<T> nEx = mk<T>(C * (Ex.x - h * (nx * nEr + mx * mEr)) - S * cBxi,
+                              C * (Ex.y - h * (nx * nEi + mx * mEi)) + S * cBxr);
+    const cplx<T> nEy = mk<T>(C * (Ey.x - h * (ny * nEr + my * mEr)) - S * cByi,
+                              C * (Ey.y - h * (ny * nEi + my * mEi)) + S * cByr);
+    const cplx<T> nEz = mk<T>(C * (Ez.x - h * (nz * nEr + mz * mEr)) - S * cBzi,
+                              C * (Ez.y - h * (nz * nEi + mz * mEi)) + S * cBzr);
+    Bx = mk<T>(C * Bx.x + S * cExi, C * Bx.y - S * cExr);
+    By = mk<T>(C * By.x + S * cEyi, C * By.y - S * cEyr);
+    Bz = mk<T>(C * Bz.x + S * cEzi, C * Bz.y - S * cEzr);
+    Ex = nEx; Ey = nEy; Ez = nEz;
+}
+
 }  // namespace psatd

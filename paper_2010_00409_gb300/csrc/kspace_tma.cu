@@ -27,12 +27,17 @@ namespace {
 //     r = q N2 + k2 <-> kz = (t + N2 q) + N1 k2) is stored back at the same
 //     positions (r, t), so the per-mode update and the first read of the inverse
 //     touch only the thread's own positions and need no barrier.
-template <typename T, int N1, int N2, int W, bool SPECTRAL_OUT>
+// HALF: the storage holds the half spectrum of real fields in the slot order of
+// the real-field plane kernels (x extent = Nx/2 slots): the slot's wave number
+// and octant index come from tables (kxs, slot_ax), modes on the y or z
+// Nyquist planes take the mean update that keeps the field real, and slot 0
+// (k_x = 0 packed with the x Nyquist mode) is left to kspace_x0_kernel.
+template <typename T, int N1, int N2, int W, bool SPECTRAL_OUT, bool HALF>
 __global__ void __launch_bounds__(W * N2)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
                   const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
                   const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err,
-                  bool project_b) {
+                  bool project_b, const int* __restrict__ slot_ax, int coef_nx) {
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
@@ -67,8 +72,8 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     // conjugates with k1 = j) and the per-mode coefficients of this thread's modes
     cplx<T> twr[N1];
     static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
-    const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
-    const int ax = min(ix, Nx - ix), ay = min(y, Ny - y);
+    const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
+    const int ax = HALF ? slot_ax[ix] : min(ix, Nx - ix), ay = min(y, Ny - y);
     const T kx = kxs[ix], ky = kys[y];
     ModeCoef<T> mc[N1];
     T kzr[N1];
@@ -139,7 +144,14 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         cplx<T> Ex = o[0], Ey = o[SLOT], Ez = o[2 * SLOT];
         cplx<T> Bx = o[3 * SLOT], By = o[4 * SLOT], Bz = o[5 * SLOT];
         const ModeCoef<T> m = mc[r];
-        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S, project_b);
+        if constexpr (HALF) {
+            constexpr int q = r / N2, k2 = r % N2;
+            const bool fz = ((j + N2 * q) + N1 * k2) == Nz / 2;
+            rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, false,
+                                y == Ny / 2, fz, m.C, m.S);
+        } else {
+            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S, project_b);
+        }
         o[0] = Ex; o[SLOT] = Ey; o[2 * SLOT] = Ez;
         o[3 * SLOT] = Bx; o[4 * SLOT] = By; o[5 * SLOT] = Bz;
     });
@@ -202,21 +214,25 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
             constexpr int b = decltype(bc)::value;
             reg_dft<T, +1, N1>(v[b]);
             cplx<T>* p = base + (q0 + b) * cstride;
-            static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
+            if (!HALF || ix != 0)
+                static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
         });
     }
 }
 
 template <typename T, int N1, int N2, int W>
 cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s, bool spectral_out, bool project_b) {
+                              int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
-    auto k = spectral_out ? kspace_tma_kernel<T, N1, N2, W, true> : kspace_tma_kernel<T, N1, N2, W, false>;
+    auto k = half ? kspace_tma_kernel<T, N1, N2, W, false, true>
+                  : (spectral_out ? kspace_tma_kernel<T, N1, N2, W, true, false>
+                                  : kspace_tma_kernel<T, N1, N2, W, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((long long)g.Ny * (g.Nx / W));
-    k<<<blocks, W * N2, smem, s>>>(map, data, g.Nx, g.Ny, tb.tw[2], tb.k[0], tb.k[1], tb.k[2], tb.coef, err,
-                                   project_b);
+    const int nx = half ? g.Nx / 2 : g.Nx;             // complex elements per stored row
+    const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W));
+    k<<<blocks, W * N2, smem, s>>>(map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
+                                   tb.coef, err, project_b, half ? half->ax : nullptr, g.Nx / 2 + 1);
     return cudaGetLastError();
 }
 
@@ -247,13 +263,13 @@ template <typename T> constexpr int kspace_tma_width() { return 64 / (int)sizeof
 
 template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
-                              int* err, cudaStream_t s, bool spectral_out, bool project_b) {
+                              int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     constexpr int W = kspace_tma_width<T>();
-    if (g.Nx % W != 0) return cudaErrorNotSupported;
+    if ((half ? g.Nx / 2 : g.Nx) % W != 0 || (half && (spectral_out || project_b))) return cudaErrorNotSupported;
     switch (g.Nz) {
-        case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s, spectral_out, project_b);
-        case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s, spectral_out, project_b);
-        case 256: return kspace_tma_launch<T, 16, 16, W>(map, data, g, tb, err, s, spectral_out, project_b);
+        case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);
+        case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);
+        case 256: return kspace_tma_launch<T, 16, 16, W>(map, data, g, tb, err, s, spectral_out, project_b, half);
         default: return cudaErrorNotSupported;
     }
 }
@@ -263,7 +279,7 @@ int kspace_tma_box_x(int prec) { return prec == 64 ? kspace_tma_width<double>() 
 // z-extent of one copy box: the whole pencil (0 if Nz has no plan here)
 int kspace_tma_box_z(int Nz) { return (Nz == 64 || Nz == 128 || Nz == 256) ? Nz : 0; }
 
-template cudaError_t launch_kspace_tma<float>(const CUtensorMap&, cplx<float>*, const GridGeom&, const Tables<float>&, int*, cudaStream_t, bool, bool);
-template cudaError_t launch_kspace_tma<double>(const CUtensorMap&, cplx<double>*, const GridGeom&, const Tables<double>&, int*, cudaStream_t, bool, bool);
+template cudaError_t launch_kspace_tma<float>(const CUtensorMap&, cplx<float>*, const GridGeom&, const Tables<float>&, int*, cudaStream_t, bool, bool, const HalfSlots<float>*);
+template cudaError_t launch_kspace_tma<double>(const CUtensorMap&, cplx<double>*, const GridGeom&, const Tables<double>&, int*, cudaStream_t, bool, bool, const HalfSlots<double>*);
 
 }  // namespace psatd

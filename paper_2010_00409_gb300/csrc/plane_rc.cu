@@ -1,0 +1,291 @@
+// Plane transforms of REAL fields (FP32, 256 x 256 planes) for the real-storage
+// step: one HBM read and one write per x-y plane, in place.
+//
+// A real row x[0..256) is read as 128 complex z[n] = x[2n] + i x[2n+1].  Its
+// 128-point transform is split as n = j + 8 n1, k = k1 + 16 k2 (j < 8, n1 < 16,
+// k1 < 16, k2 < 8):  stage A = 16-point DFT over n1 and twiddle W_128^{j k1}
+// (in the registers of lane j), stage B = 8-point DFT over j.  The real-to-
+// complex step pairs Z[k] with Z[128-k]:
+//   X[k] = (Z[k] + conj Z[128-k])/2 + W_256^k (Z[k] - conj Z[128-k])/(2i),
+// and X[0], X[128] (both real) share slot 0 as X[0] + i X[128].
+//
+// A cluster of 8 blocks owns one plane.  Block r owns the stage-A outputs with
+// k1 in {r, 16-r} (block 0: {0, 8}); those are exactly the k that pair with each
+// other, so the exchange between the blocks (distributed shared memory) is also
+// the transpose of the 128-point transform.  Block r stores its 16 spectral
+// columns at slots 16 r .. 16 r + 15: slot p = 16 r + 8 s + k2 holds
+// X[k1(r, s) + 16 k2] with k1(r, 0) = r, k1(r, 1) = 16 - r (k1(0, 1) = 8).
+// The spectrum between the plane kernels is kept in this slot order; the
+// k-space kernels read the slot's wave number from a table.
+//
+// Forward (r2c):   phase 1  rows of block r (32 per block): stage A, scatter to
+//                           the owners of k1;  cluster barrier;
+//                  phase 2a one thread per row: stage B and the r2c pairing,
+//                           in place;
+//                  phase 2b the 16 columns along y (256 points), in place
+//                           exchange, stores of 128-byte row segments.
+// Inverse (c2r) is the mirror: inverse y on the block's 16 columns, the c2r
+// pairing and inverse stage B per row, scatter to the owners of the rows,
+// cluster barrier, inverse stage A per row, stores.
+//
+// Shared memory: one 32 KB tile per block, swizzled (column ^ (row & 15)) so
+// that every access pattern above runs at two wavefronts per warp.
+#include <cooperative_groups.h>
+
+#include "fft_reg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace psatd {
+
+namespace {
+
+constexpr int kRcThreads = 256;
+constexpr int kRcC = 8;               // blocks per plane (cluster size)
+constexpr int kM = 128;               // complex elements per row
+constexpr int kNy = 256;
+
+// tile [256][16] and, in the inverse, [32][128]
+__device__ __forceinline__ int sw16(int row, int col) { return row * 16 + (col ^ (row & 15)); }
+__device__ __forceinline__ int sw128(int row, int col) { return row * 128 + (col ^ (row & 15)); }
+
+constexpr int owner_of(int k1) { return (k1 == 0 || k1 == 8) ? 0 : (k1 < 8 ? k1 : 16 - k1); }
+constexpr int half_of(int k1) { return (k1 == 0) ? 0 : (k1 == 8 ? 1 : (k1 < 8 ? 0 : 1)); }
+
+// W_256^k for compile-time k
+template <int K> __device__ __forceinline__ float2 w256() {
+    return make_float2((float)ct_cos2pi(K, 256), (float)-ct_sin2pi(K, 256));
+}
+
+// r2c pairing of Z = Z[k] and P = Z[128-k] with w = W_256^k: returns X[k] in *a
+// and X[128-k] in *b.
+__device__ __forceinline__ void r2c_pair(float2 Z, float2 P, float2 w, float2* a, float2* b) {
+    const float2 A = make_float2(0.5f * (Z.x + P.x), 0.5f * (Z.y - P.y));
+    const float2 Bv = make_float2(0.5f * (Z.y + P.y), -0.5f * (Z.x - P.x));
+    const float2 T = cmul(w, Bv);
+    *a = make_float2(A.x + T.x, A.y + T.y);
+    *b = make_float2(A.x - T.x, T.y - A.y);           // conj(A - T)
+}
+
+// c2r pairing of X = X[k] and P = X[128-k] with w = W_256^k (the inverse uses
+// W_256^{-k} = conj w): Z2[k] in *a, Z2[128-k] in *b, where
+//   Z2[k] = (X + conj P) + i W^{-k} (X - conj P)
+__device__ __forceinline__ void c2r_pair(float2 X, float2 P, float2 w, float2* a, float2* b) {
+    const float2 Pp = make_float2(X.x + P.x, X.y - P.y);
+    const float2 Q = make_float2(X.x - P.x, X.y + P.y);
+    const float2 U = cmulc(Q, w);
+    *a = make_float2(Pp.x - U.y, Pp.y + U.x);
+    *b = make_float2(Pp.x + U.y, U.x - Pp.y);         // conj(Pp - i U)
+}
+
+__global__ void __launch_bounds__(kRcThreads)
+plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.barrier_arrive();                          // wait for all blocks before the first remote store
+    const int r = (int)cluster.block_rank();
+    float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
+    const int tid = threadIdx.x;
+
+    // ---------------- phase 1: stage A of rows 32 r .. 32 r + 31, scatter by k1
+    {
+        const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
+        const int y = 32 * r + w + 8 * g;              // rows of a warp alternate in bit 3 (bank spread)
+        const float2* p = plane + (size_t)y * kM;
+        float2 v[16];
+        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = p[j + 8 * decltype(nc)::value]; });
+        reg_dft<float, -1, 16>(v);
+        static_for<1, 16>([&](auto kc) {
+            constexpr int k1 = decltype(kc)::value;
+            if (j) v[k1] = cmul(v[k1], twx[2 * j * k1]);
+        });
+        cluster.barrier_wait();
+        static_for<0, 16>([&](auto kc) {
+            constexpr int k1 = decltype(kc)::value;
+            float2* dst = cluster.map_shared_rank(tile, owner_of(k1));
+            dst[sw16(y, half_of(k1) * 8 + j)] = v[k1];
+        });
+    }
+    cluster.sync();
+
+    // ---------------- phase 2a: stage B and the r2c pairing, one row per thread
+    {
+        const int y = tid;
+        float2 a[2][8];
+        static_for<0, 2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<0, 8>([&](auto jc) { a[s][decltype(jc)::value] = tile[sw16(y, s * 8 + decltype(jc)::value)]; });
+            reg_dft<float, -1, 8>(a[s]);               // a[s][k2] = Z[k1(r, s) + 16 k2]
+        });
+        float2 o[2][8];
+        if (r == 0) {
+            o[0][0] = make_float2(a[0][0].x + a[0][0].y, a[0][0].x - a[0][0].y);   // X[0] + i X[128]
+            static_for<1, 5>([&](auto kc) {            // k = 16 k2 pairs with 16 (8 - k2)
+                constexpr int k2 = decltype(kc)::value;
+                r2c_pair(a[0][k2], a[0][8 - k2], w256<16 * k2>(), &o[0][k2], &o[0][8 - k2]);
+            });
+            static_for<0, 4>([&](auto kc) {            // k = 8 + 16 k2 pairs with 8 + 16 (7 - k2)
+                constexpr int k2 = decltype(kc)::value;
+                r2c_pair(a[1][k2], a[1][7 - k2], w256<8 + 16 * k2>(), &o[1][k2], &o[1][7 - k2]);
+            });
+        } else {
+            static_for<0, 8>([&](auto kc) {            // k = r + 16 k2 pairs with (16 - r) + 16 (7 - k2)
+                constexpr int k2 = decltype(kc)::value;
+                r2c_pair(a[0][k2], a[1][7 - k2], twx[r + 16 * k2], &o[0][k2], &o[1][7 - k2]);
+            });
+        }
+        static_for<0, 2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<0, 8>([&](auto kc) { tile[sw16(y, s * 8 + decltype(kc)::value)] = o[s][decltype(kc)::value]; });
+        });
+    }
+    __syncthreads();
+
+    // ---------------- phase 2b: 256-point transforms of the 16 columns along y
+    {
+        const int c = tid & 15, jy = tid >> 4;
+        float2 v[16];
+        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = tile[sw16(jy + 16 * decltype(nc)::value, c)]; });
+        stage_a_fwd<float, -1, 16, 16>(v, jy, twy);
+        // element (k1, jy) at row 16 k1 + jy: the positions this thread just read
+        static_for<0, 16>([&](auto kc) { tile[sw16(16 * decltype(kc)::value + jy, c)] = v[decltype(kc)::value]; });
+        __syncthreads();
+        static_for<0, 16>([&](auto jc) { v[decltype(jc)::value] = tile[sw16(16 * jy + decltype(jc)::value, c)]; });
+        reg_dft<float, -1, 16>(v);                     // v[k2] = Y[jy + 16 k2]
+        float2* out = plane + 16 * r + c;
+        static_for<0, 16>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            out[(size_t)(jy + 16 * k2) * kM] = v[k2];
+        });
+    }
+}
+
+__global__ void __launch_bounds__(kRcThreads)
+plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = (int)cluster.block_rank();
+    float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
+    const int tid = threadIdx.x;
+
+    // ---------------- phase 1: inverse y on slots 16 r .. 16 r + 15
+    {
+        const int c = tid & 15, jy = tid >> 4;
+        const float2* in = plane + 16 * r + c;
+        float2 v[16];
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = in[(size_t)(jy + 16 * decltype(kc)::value) * kM]; });
+        reg_dft<float, +1, 16>(v);                     // over k2, k1 = jy
+        static_for<0, 16>([&](auto nc) {
+            constexpr int n2 = decltype(nc)::value;
+            float2 val = v[n2];
+            if (n2 > 0 && jy > 0) val = cmulc(val, twy[n2 * jy]);
+            tile[sw16(16 * jy + n2, c)] = val;          // element (k1 = jy, n2)
+        });
+        __syncthreads();
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[sw16(16 * decltype(kc)::value + jy, c)]; });
+        reg_dft<float, +1, 16>(v);                     // v[n1] = y[jy + 16 n1]
+        static_for<0, 16>([&](auto nc) { tile[sw16(jy + 16 * decltype(nc)::value, c)] = v[decltype(nc)::value]; });
+    }
+    __syncthreads();
+
+    // ---------------- phase 1b: c2r pairing and inverse stage B, one row per thread
+    {
+        const int y = tid;
+        float2 x[2][8];
+        static_for<0, 2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<0, 8>([&](auto kc) { x[s][decltype(kc)::value] = tile[sw16(y, s * 8 + decltype(kc)::value)]; });
+        });
+        cluster.barrier_arrive();                      // this block's tile is free for the remote stores
+        float2 z[2][8];
+        if (r == 0) {
+            z[0][0] = make_float2(x[0][0].x + x[0][0].y, x[0][0].x - x[0][0].y);   // X[0] = re, X[128] = im
+            static_for<1, 5>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                c2r_pair(x[0][k2], x[0][8 - k2], w256<16 * k2>(), &z[0][k2], &z[0][8 - k2]);
+            });
+            static_for<0, 4>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                c2r_pair(x[1][k2], x[1][7 - k2], w256<8 + 16 * k2>(), &z[1][k2], &z[1][7 - k2]);
+            });
+        } else {
+            static_for<0, 8>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                c2r_pair(x[0][k2], x[1][7 - k2], twx[r + 16 * k2], &z[0][k2], &z[1][7 - k2]);
+            });
+        }
+        const int k1s[2] = {r == 0 ? 0 : r, r == 0 ? 8 : 16 - r};
+        static_for<0, 2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            reg_dft<float, +1, 8>(z[s]);               // over k2 -> j
+            const int k1 = k1s[s];
+            static_for<1, 8>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if (k1) z[s][j] = cmulc(z[s][j], twx[2 * j * k1]);
+            });
+        });
+        cluster.barrier_wait();
+        float2* dst = cluster.map_shared_rank(tile, y >> 5);
+        const int yl = y & 31;
+        static_for<0, 2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<0, 8>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                dst[sw128(yl, k1s[s] * 8 + j)] = z[s][j];
+            });
+        });
+    }
+    cluster.sync();
+
+    // ---------------- phase 3: inverse stage A of rows 32 r .. 32 r + 31
+    {
+        const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
+        const int yl = w + 8 * g;
+        float2 v[16];
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[sw128(yl, decltype(kc)::value * 8 + j)]; });
+        reg_dft<float, +1, 16>(v);                     // v[n1] = z[j + 8 n1]
+        float2* p = plane + (size_t)(32 * r + yl) * kM;
+        static_for<0, 16>([&](auto nc) { p[j + 8 * decltype(nc)::value] = v[decltype(nc)::value]; });
+    }
+}
+
+}  // namespace
+
+bool plane_rc_supported(int prec, const GridGeom& g) { return prec == 32 && g.Nx == 256 && g.Ny == 256; }
+
+// Real-field plane transform of ncomp components (dir < 0: r2c + y, dir > 0:
+// inverse y + c2r) of real FP32 fields [ncomp][Nz][256][256], in place.
+cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
+                            cudaStream_t s) {
+    if (!plane_rc_supported(32, g)) return cudaErrorNotSupported;
+    const size_t smem = (size_t)kM * kNy / kRcC * sizeof(float2);    // 32 KB
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((long long)ncomp * g.Nz * kRcC), 1, 1);
+    cfg.blockDim = dim3(kRcThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kRcC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    float2* d = reinterpret_cast<float2*>(data);
+    if (dir < 0) return cudaLaunchKernelEx(&cfg, plane_r2c_kernel, d, tb.tw[0], tb.tw[1]);
+    return cudaLaunchKernelEx(&cfg, plane_c2r_kernel, d, tb.tw[0], tb.tw[1]);
+}
+
+// Slot order of the spectra the plane kernels leave in storage: the x mode
+// index 0..127 held by slot p (slot 0 also holds the Nyquist mode 128).
+int plane_rc_slot_mode(int p) {
+    const int r = p / 16, s = (p / 8) & 1, k2 = p & 7;
+    const int k1 = r == 0 ? (s ? 8 : 0) : (s ? 16 - r : r);
+    return k1 + 16 * k2;
+}
+
+}  // namespace psatd

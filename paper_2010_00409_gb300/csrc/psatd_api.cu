@@ -83,6 +83,9 @@ struct psatd_ctx {
     void* fields = nullptr;
     size_t field_bytes = 0;
     bool own_fields = false;
+    bool real_fields = false;           // real float32 storage (PSATD_FLAG_REAL_FIELDS)
+    DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
+    DevBuf slot_k, slot_ax;             // real fields: k_x and |m_x| per half-spectrum slot
 
     // tables (device)
     DevBuf tw[3], k[3], coef;
@@ -100,6 +103,7 @@ struct psatd_ctx {
     // tensor map of the field storage for the copy-engine-fed k-space kernel
     alignas(64) CUtensorMap field_map;
     void* field_map_ptr = nullptr;      // storage the map was encoded for
+    bool field_map_real = false;        // ... and whether as a real-field half spectrum
     bool field_map_ok = false;
     int* dev_err = nullptr;             // device error word (bits of psatd::DeviceError)
 
@@ -141,6 +145,8 @@ psatd_status cuda_fail(psatd_ctx* c, cudaError_t e, const char* where) {
 
 size_t cplx_size(int prec) { return prec == 64 ? 16 : 8; }
 size_t n_cells(const psatd_grid& g) { return (size_t)g.Nx * g.Ny * g.Nz; }
+// bytes of one stored field value
+size_t value_size(const psatd_ctx* c) { return c->real_fields ? sizeof(float) : cplx_size(c->prec); }
 
 void free_buf(DevBuf& b) {
     if (b.p) cudaFree(b.p);
@@ -321,22 +327,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // (Re)encode the field tensor map when the storage changed; false if the
 // copy-engine path does not apply to this grid.
 bool ensure_field_map(psatd_ctx* c) {
-    if (c->field_map_ptr == c->fields) return c->field_map_ok;
+    if (c->field_map_ptr == c->fields && c->field_map_real == c->real_fields) return c->field_map_ok;
     c->field_map_ptr = c->fields;
+    c->field_map_real = c->real_fields;
     c->field_map_ok = false;
     const psatd_grid& g = c->grid;
     if (g.Nz > 256 || !c->dev_err) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t es = cplx_size(c->prec), xw = es / 8;
-    const cuuint64_t dims[4] = {(cuuint64_t)g.Nx * xw, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, 6};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.Nx * es, (cuuint64_t)g.Nx * g.Ny * es,
-                                   (cuuint64_t)g.Nx * g.Ny * g.Nz * es};
+    const cuuint64_t nx = c->real_fields ? g.Nx / 2 : g.Nx;     // complex values per stored row
+    const cuuint64_t dims[4] = {nx * xw, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz, 6};
+    const cuuint64_t strides[3] = {nx * es, nx * g.Ny * es, nx * g.Ny * g.Nz * es};
     const int bz = kspace_tma_box_z(g.Nz);
     if (bz == 0) return false;
     const cuuint32_t box[4] = {(cuuint32_t)kspace_tma_box_x(c->prec), 1, (cuuint32_t)bz, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    if (dims[0] < box[0] || (g.Nx * es) % 16 != 0) return false;
+    if (dims[0] < box[0] || (nx * es) % 16 != 0) return false;
     CUresult r = enc(&c->field_map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, c->fields, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -456,6 +463,81 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     return cudaSuccess;
 }
 
+// One real-field step: r2c plane transforms, the half-spectrum k-space pass,
+// the packed slot-0 pass, c2r plane transforms.
+cudaError_t spectral_pass_real(psatd_ctx* c) {
+    const GridGeom g = geom(c);
+    const Tables<float> tb = tables<float>(c);
+    float* f = static_cast<float*>(c->fields);
+    cudaError_t e = timed(c, PSATD_KERNEL_PLANE_XY, [&] {
+        ++c->launches;
+        return launch_plane_rc(f, 6, g, tb, -1, c->stream);
+    });
+    if (e != cudaSuccess) return e;
+    if (!ensure_field_map(c)) return cudaErrorNotSupported;
+    const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p), static_cast<const int*>(c->slot_ax.p)};
+    e = timed(c, PSATD_KERNEL_KSPACE, [&] {
+        ++c->launches;
+        return launch_kspace_tma<float>(c->field_map, reinterpret_cast<cplx<float>*>(f), g, tb, c->dev_err, c->stream,
+                                        false, false, &hs);
+    });
+    if (e != cudaSuccess) return e;
+    e = timed(c, PSATD_KERNEL_KSPACE_X0, [&] {
+        ++c->launches;
+        return launch_kspace_x0(reinterpret_cast<float2*>(f), g, tb, c->stream);
+    });
+    if (e != cudaSuccess) return e;
+    return timed(c, PSATD_KERNEL_PLANE_XY, [&] {
+        ++c->launches;
+        return launch_plane_rc(f, 6, g, tb, +1, c->stream);
+    });
+}
+
+// Real fields: operations written for complex storage run on the context's
+// complex scratch copy while a ComplexView is alive.
+struct ComplexView {
+    psatd_ctx* c;
+    void* fields;
+    size_t bytes;
+    explicit ComplexView(psatd_ctx* cc) : c(cc), fields(cc->fields), bytes(cc->field_bytes) {
+        c->fields = c->cscratch.p;
+        c->field_bytes = c->cscratch.bytes;
+        c->real_fields = false;
+    }
+    ~ComplexView() {
+        c->fields = fields;
+        c->field_bytes = bytes;
+        c->real_fields = true;
+    }
+};
+
+// Allocate the complex scratch copy; with widen, fill it from the real fields.
+psatd_status ensure_scratch(psatd_ctx* c, bool widen) {
+    const size_t n = 6 * n_cells(c->grid);
+    CK(c, ensure_buf(c->cscratch, n * sizeof(float2)));
+    if (widen) {
+        CK(c, launch_widen(static_cast<const float*>(c->fields), static_cast<float2*>(c->cscratch.p), n, c->stream));
+        ++c->launches;
+    }
+    return PSATD_OK;
+}
+
+psatd_status upload_slot_tables(psatd_ctx* c) {
+    const int nh = c->grid.Nx / 2;
+    std::vector<float> k(nh);
+    std::vector<int> ax(nh);
+    for (int p = 0; p < nh; ++p) {
+        const int m = plane_rc_slot_mode(p);
+        ax[p] = m;
+        k[p] = (float)(kTwoPi * (double)m / (c->grid.Nx * c->grid.dx));
+    }
+    CK(c, ensure_buf(c->slot_k, nh * sizeof(float)));
+    CK(c, ensure_buf(c->slot_ax, nh * sizeof(int)));
+    CK(c, cudaMemcpy(c->slot_k.p, k.data(), nh * sizeof(float), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->slot_ax.p, ax.data(), nh * sizeof(int), cudaMemcpyHostToDevice));
+    return PSATD_OK;
+}
+
 double F_series(double t0) {
     const double t2 = t0 * t0;
     return t2 / 4 - t2 * t2 / 48 + t2 * t2 * t2 / 960;
@@ -541,6 +623,10 @@ psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mappin
     if (!is_finite(dt)) return fail(nullptr, PSATD_ERR_ARG, "dt must be finite");
     if (mapping && !(is_finite(mapping->R0) && is_finite(mapping->L) && mapping->L >= 0))
         return fail(nullptr, PSATD_ERR_ARG, "mapping R0, L must be finite, L >= 0");
+    const bool real = (flags & PSATD_FLAG_REAL_FIELDS) != 0;
+    if (real && !(precision == 32 && grid->Nx == 256 && grid->Ny == 256 &&
+                  (grid->Nz == 64 || grid->Nz == 128 || grid->Nz == 256)))
+        return fail(nullptr, PSATD_ERR_ARG, "real fields need precision 32 and a 256 x 256 x {64, 128, 256} grid");
 
     psatd_ctx* c = new (std::nothrow) psatd_ctx();
     if (!c) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
@@ -548,6 +634,7 @@ psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mappin
     if (mapping) c->mapping = *mapping;
     c->dt = dt;
     c->prec = precision;
+    c->real_fields = real;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     for (int a = 0; a < 3; ++a) make_plan(Ns[a], &c->plan[a]);
 
@@ -556,13 +643,14 @@ psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mappin
     if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGetDevice");
     if (st == PSATD_OK) st = precision == 64 ? upload_axis_tables<double>(c) : upload_axis_tables<float>(c);
     if (st == PSATD_OK) st = set_coef(c, dt);
+    if (st == PSATD_OK && real) st = upload_slot_tables(c);
     if (st == PSATD_OK) {
         e = cudaMalloc(&c->dev_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(error word)");
     }
     if (st == PSATD_OK && !(flags & PSATD_FLAG_NO_FIELD_ALLOC)) {
-        const size_t bytes = 6 * n_cells(*grid) * cplx_size(precision);
+        const size_t bytes = 6 * n_cells(*grid) * value_size(c);
         e = cudaMalloc(&c->fields, bytes);
         if (e != cudaSuccess) {
             c->fields = nullptr;
@@ -594,6 +682,7 @@ void psatd_destroy(psatd_ctx* c) {
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
     free_buf(c->coef_T);
+    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_ax);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
@@ -622,7 +711,7 @@ psatd_status psatd_set_mapping(psatd_ctx* c, const psatd_mapping* m) {
 psatd_status psatd_bind_fields(psatd_ctx* c, void* dev_ptr, size_t bytes) {
     psatd_status st = check_ctx(c, false);
     if (st) return st;
-    const size_t need = 6 * n_cells(c->grid) * cplx_size(c->prec);
+    const size_t need = 6 * n_cells(c->grid) * value_size(c);
     if (!dev_ptr) return fail(c, PSATD_ERR_ARG, "NULL field pointer");
     if (bytes < need) return fail(c, PSATD_ERR_ARG, "field storage too small");
     if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0) return fail(c, PSATD_ERR_ARG, "field storage must be 256-byte aligned");
@@ -655,7 +744,7 @@ static psatd_status copy_field(psatd_ctx* c, int comp, void* dst, const void* sr
     if (comp < -1 || comp > 5) return fail(c, PSATD_ERR_ARG, "comp must be -1..5");
     if (!on_device && capturing(c)) return fail(c, PSATD_ERR_STATE, "host copies are not allowed while a batch is being captured");
     if (!(to_lib ? src : dst)) return fail(c, PSATD_ERR_ARG, "NULL buffer");
-    const size_t per = n_cells(c->grid) * cplx_size(c->prec);
+    const size_t per = n_cells(c->grid) * value_size(c);
     const size_t bytes = comp < 0 ? 6 * per : per;
     char* lib = static_cast<char*>(c->fields) + (comp < 0 ? 0 : comp * per);
     cudaMemcpyKind kind;
@@ -680,6 +769,20 @@ psatd_status psatd_get_field(psatd_ctx* c, int comp, void* dst, int dst_on_devic
 psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
+    if (c->real_fields) {
+        // the complex pulse (and projection) in the scratch copy, then its real part
+        st = ensure_scratch(c, false);
+        if (st) return st;
+        {
+            ComplexView v(c);
+            st = psatd_init_pulse(c, p);
+        }
+        if (st) return st;
+        CK(c, launch_narrow(static_cast<const float2*>(c->cscratch.p), static_cast<float*>(c->fields),
+                            6 * n_cells(c->grid), c->stream));
+        ++c->launches;
+        return PSATD_OK;
+    }
     if (!p) return fail(c, PSATD_ERR_ARG, "NULL pulse");
     if (p->kind != PSATD_PULSE_FLAT_TOP && p->kind != PSATD_PULSE_GAUSSIAN)
         return fail(c, PSATD_ERR_ARG, "unknown pulse kind");
@@ -739,8 +842,9 @@ psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
     psatd_batch* b = capturing(c);
     if (b && c->prof_on) return fail(c, PSATD_ERR_STATE, "profiling must be off while capturing a batch");
     for (int s = 0; s < n_steps; ++s) {
-        cudaError_t e = c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0)
-                                      : spectral_pass<float>(c, KS_ROTATE, 0.0);
+        cudaError_t e = c->real_fields ? spectral_pass_real(c)
+                        : c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0)
+                                        : spectral_pass<float>(c, KS_ROTATE, 0.0);
         if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
         if (!b) c->t += c->dt;
     }
@@ -753,6 +857,7 @@ psatd_status psatd_fft(psatd_ctx* c, int direction) {
     if (st) return st;
     if (direction != PSATD_FORWARD && direction != PSATD_INVERSE)
         return fail(c, PSATD_ERR_ARG, "direction must be PSATD_FORWARD or PSATD_INVERSE");
+    if (c->real_fields) return fail(c, PSATD_ERR_STATE, "psatd_fft works on complex field storage only");
     cudaError_t e = c->prec == 64 ? fft3d<double>(c, static_cast<cplx<double>*>(c->fields), 6, direction)
                                   : fft3d<float>(c, static_cast<cplx<float>*>(c->fields), 6, direction);
     if (e != cudaSuccess) return cuda_fail(c, e, "fft launch");
@@ -763,6 +868,13 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
                                       double z0, double z1, int comp_mask, void* dst, int dst_on_device) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
+    if (c->real_fields) {
+        if (capturing(c)) return fail(c, PSATD_ERR_STATE, "sample_focal_plane is not captured into batches");
+        st = ensure_scratch(c, true);
+        if (st) return st;
+        ComplexView v(c);
+        return psatd_sample_focal_plane(c, x_phys, ny, nz, y0, y1, z0, z1, comp_mask, dst, dst_on_device);
+    }
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
     if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
@@ -808,6 +920,7 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
                                   int dst_on_device) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
+    if (c->real_fields) return fail(c, PSATD_ERR_STATE, "the one-shot path works on complex field storage only");
     if (!is_finite(T)) return fail(c, PSATD_ERR_ARG, "T must be finite");
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
@@ -883,6 +996,12 @@ psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
     if (st) return st;
     if (capturing(c)) return fail(c, PSATD_ERR_STATE, "not allowed while a batch is being captured");
     if (!out) return fail(c, PSATD_ERR_ARG, "NULL out");
+    if (c->real_fields) {
+        st = ensure_scratch(c, true);
+        if (st) return st;
+        ComplexView v(c);
+        return psatd_diagnostics(c, out);
+    }
     const size_t n = n_cells(c->grid);
     const size_t es = cplx_size(c->prec);
     CK(c, ensure_buf(c->diag_spec, 3 * n * es));
@@ -1020,6 +1139,12 @@ psatd_status psatd_autotune(psatd_ctx* c, int trial_steps, int* path_out, int* s
     psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (capturing(c)) return fail(c, PSATD_ERR_STATE, "cannot tune inside a batch capture");
+    if (c->real_fields) {                      // one kernel set: nothing to choose
+        if (path_out) *path_out = PSATD_PATH_AUTO;
+        if (shift_out) *shift_out = 0;
+        if (ms_out) *ms_out = -1.0;
+        return PSATD_OK;
+    }
     if (trial_steps < 1) trial_steps = 2;
     const auto key = std::make_tuple(c->grid.Nx, c->grid.Ny, c->grid.Nz, c->prec);
     {
@@ -1120,7 +1245,7 @@ psatd_status psatd_profile_read(psatd_ctx* c, int kind, double* total_ms, long l
 const char* psatd_kernel_name(int kind) {
     static const char* names[PSATD_KERNEL_KINDS] = {"fft_x", "fft_y", "fft_z", "kspace_z",
                                                     "init_pulse", "sample_plane", "diagnostics",
-                                                    "plane_xy"};
+                                                    "plane_xy", "kspace_x0"};
     return (kind >= 0 && kind < PSATD_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 

@@ -19,6 +19,7 @@ ERR_ARG, ERR_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -
 FLAT_TOP, GAUSSIAN = 0, 1
 FORWARD, INVERSE = -1, +1
 FLAG_NO_FIELD_ALLOC = 1
+FLAG_REAL_FIELDS = 2
 
 # every symbol include/psatd.h declares
 EXPORTS = (
@@ -37,7 +38,7 @@ EXPORTS = (
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
 KERNEL_KINDS = ("fft_x", "fft_y", "fft_z", "kspace_z", "init_pulse", "sample_plane", "diagnostics",
-                "plane_xy")
+                "plane_xy", "kspace_x0")
 
 
 class PsatdGrid(C.Structure):
@@ -300,22 +301,27 @@ def gemm_bf16(A, B, Cout, alpha=1.0, beta=0.0, ksplit=1, stream=None):
 
 class Context:
     """One periodic box on the current CUDA device; fields are a torch tensor
-    [6, Nz, Ny, Nx] (complex64 or complex128) bound to the library."""
+    [6, Nz, Ny, Nx] (complex64 or complex128, or float32 with real=True) bound
+    to the library.  Sampled planes are complex of the context's precision."""
 
     def __init__(self, grid, mapping=None, dt: float = 0.0, precision: int = 64, stream=None,
-                 fields=None):
+                 fields=None, real: bool = False):
         import torch
         self._torch = torch
         self.grid = grid
         self.precision = precision
-        self.dtype = torch.complex128 if precision == 64 else torch.complex64
+        self.real = real
+        self.cdtype = torch.complex128 if precision == 64 else torch.complex64
+        self.dtype = torch.float32 if real else self.cdtype
+        self._np_field = np.float32 if real else (np.complex128 if precision == 64 else np.complex64)
+        self._np_sample = np.complex128 if precision == 64 else np.complex64
         dev = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         m = PsatdMapping(mapping.R0, mapping.L) if mapping is not None else None
         ptr = C.c_void_p()
+        flags = FLAG_NO_FIELD_ALLOC | (FLAG_REAL_FIELDS if real else 0)
         st = lib().psatd_init_grid(C.byref(make_grid(grid)), C.byref(m) if m is not None else None, dt,
-                                   precision, C.c_void_p(self.stream.cuda_stream), FLAG_NO_FIELD_ALLOC,
-                                   C.byref(ptr))
+                                   precision, C.c_void_p(self.stream.cuda_stream), flags, C.byref(ptr))
         _check(st, None)
         self._ptr = ptr
         if fields is None:
@@ -354,8 +360,7 @@ class Context:
     def set_field(self, comp: int, src):
         """src: numpy array (host) or torch tensor (device), layout of the storage."""
         if isinstance(src, np.ndarray):
-            want = np.complex128 if self.precision == 64 else np.complex64
-            a = np.ascontiguousarray(src, dtype=want)
+            a = np.ascontiguousarray(src, dtype=self._np_field)
             _check(lib().psatd_set_field(self._ptr, comp, a.ctypes.data_as(C.c_void_p), 0), self._ptr)
         else:
             t = src.to(self.dtype).contiguous()
@@ -365,9 +370,8 @@ class Context:
         self.set_field(-1, src)
 
     def get_field(self, comp: int = -1) -> np.ndarray:
-        want = np.complex128 if self.precision == 64 else np.complex64
         shape = (self.grid.Nz, self.grid.Ny, self.grid.Nx)
-        out = np.empty(((6,) if comp < 0 else ()) + shape, dtype=want)
+        out = np.empty(((6,) if comp < 0 else ()) + shape, dtype=self._np_field)
         _check(lib().psatd_get_field(self._ptr, comp, out.ctypes.data_as(C.c_void_p), 0), self._ptr)
         return out
 
@@ -386,12 +390,11 @@ class Context:
             mask |= 1 << c
         nc = bin(mask).count("1")
         if out is None:
-            want = np.complex128 if self.precision == 64 else np.complex64
-            out = np.empty((nc, nz, ny), dtype=want)
+            out = np.empty((nc, nz, ny), dtype=self._np_sample)
             _check(lib().psatd_sample_focal_plane(self._ptr, x_phys, ny, nz, y0, y1, z0, z1, mask,
                                                   out.ctypes.data_as(C.c_void_p), 0), self._ptr)
             return out
-        assert out.dtype == self.dtype and out.is_cuda and out.numel() >= nc * ny * nz
+        assert out.dtype == self.cdtype and out.is_cuda and out.numel() >= nc * ny * nz
         _check(lib().psatd_sample_focal_plane(self._ptr, x_phys, ny, nz, y0, y1, z0, z1, mask,
                                               C.c_void_p(out.data_ptr()), 1), self._ptr)
         return out
@@ -402,12 +405,11 @@ class Context:
             mask |= 1 << c
         nc = bin(mask).count("1")
         if out is None:
-            want = np.complex128 if self.precision == 64 else np.complex64
-            out = np.empty((nc, nz, ny), dtype=want)
+            out = np.empty((nc, nz, ny), dtype=self._np_sample)
             _check(lib().psatd_focal_one_shot(self._ptr, C.byref(make_pulse(pulse)), T, x_phys, ny, nz, y0, y1,
                                               z0, z1, mask, out.ctypes.data_as(C.c_void_p), 0), self._ptr)
             return out
-        assert out.dtype == self.dtype and out.is_cuda and out.numel() >= nc * ny * nz
+        assert out.dtype == self.cdtype and out.is_cuda and out.numel() >= nc * ny * nz
         _check(lib().psatd_focal_one_shot(self._ptr, C.byref(make_pulse(pulse)), T, x_phys, ny, nz, y0, y1, z0,
                                           z1, mask, C.c_void_p(out.data_ptr()), 1), self._ptr)
         return out

@@ -276,6 +276,20 @@ def test_tight_focus_256_full_size(lib, focus_reference, prec):
     assert d["max_div_E"] <= (1e-12 if prec == 64 else 1e-5) * d["max_E_hat"]
 
 
+def test_tight_focus_256_full_size_real_fields(lib, focus_reference):
+    """The same job with real float32 field storage (half the bytes per step)."""
+    g, m, p, n_steps, plane, dt, ref, e0 = focus_reference
+    with lib.Context(g, m, dt, 32, real=True) as ctx:
+        ctx.init_pulse(p)
+        ctx.advance(n_steps)
+        got = ctx.sample_focal_plane(plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"],
+                                     plane["z0"], plane["z1"], comps=(0, 1, 2))
+        d = ctx.diagnostics()
+    assert rel(got, ref) <= 1e-4
+    assert abs(d["energy"] / e0 - 1) <= 8 * 2.0 ** -24 * n_steps
+    assert d["max_div_E"] <= 1e-5 * d["max_E_hat"]
+
+
 # ---------------------------------------------------------------------------
 # Register-resident kernels (axis lengths 64, 128, 256, 512) against the oracle
 # and against the generic shared-memory kernels on the same inputs.
