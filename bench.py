@@ -5,8 +5,12 @@ the 256^3 mapped grid: pulse initialisation on the periodic layer, 378 PSATD
 steps to the focus t = R0/c, the 128 x 128 focal-plane sample, and the energy /
 divergence diagnostics.  The metric is PSATD cell-steps/s (cells x PSATD steps
 per second) and the fraction of the HBM roofline reached by the dominant kernel.
+The fields are stored as real float32 (the physical E and B are real; --storage
+complex times the complex64 storage instead, and the other storage is reported
+beside the headline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage real|complex]
 
 N > 1 runs one independent replica per GPU (the path does not shard); the
 value is the total work of all ranks over the slowest rank's time.
@@ -35,7 +39,9 @@ from paper_2010_00409_gb300 import workloads as W  # noqa: E402
 
 METRIC = "PSATD cell-steps/s"
 UNIT = "cell-steps/s"
-STEP_KERNELS = ("fft_x", "fft_y", "fft_z", "kspace_z", "plane_xy")
+STEP_KERNELS = ("fft_x", "fft_y", "fft_z", "kspace_z", "plane_xy", "kspace_x0")
+# algorithmic bytes per cell of one full-field sweep (six components read and written)
+SWEEP_BYTES = {"real": 48, "complex": 96}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -50,6 +56,7 @@ def args_parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--storage", choices=("real", "complex"), default="real")
     return ap.parse_args()
 
 
@@ -58,9 +65,10 @@ def dist_env():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one ncu capture of the default command at 256^3 (mean of
-# the forward and inverse launches); to be re-taken whenever that kernel changes.
-NCU_TRAFFIC_BYTES = {("plane_xy", 256): 1549.95e6}
+# dominant kernel, from one ncu capture at 256^3 (mean of the forward and
+# inverse launches), keyed by (kernel, size, storage); to be re-taken whenever
+# that kernel changes.
+NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.95e6}
 
 
 def measured_peaks():
@@ -154,20 +162,23 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(a.size),
+        "config": workload_config(a.size, a.storage),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config(size):
+def workload_config(size, storage="real"):
     g, m, p, n_steps, plane = W.tight_focus_workload(N=size)
+    vb = 4 if storage == "real" else 8
     return {"workload": "tight focus f=1, 2-cycle Gaussian at 800 nm, R0=20 lambda, %d^3 mapped grid, "
                         "%d PSATD steps to focus + 128x128 focal plane + diagnostics" % (size, n_steps),
             "grid": [g.Nx, g.Ny, g.Nz], "psatd_steps_per_job": n_steps, "precision": "fp32 storage/arithmetic, "
-            "fp64 tables/coordinates/reductions", "layout": "SoA [6][Nz][Ny][Nx] complex64",
-            "l2": "inputs larger than L2 (field %.0f MB > 129 MB L2)" % (6 * g.cells * 8 / 1e6),
+            "fp64 tables/coordinates/reductions",
+            "layout": "SoA [6][Nz][Ny][Nx] " + ("float32 (real fields; half spectrum between kernels)"
+                                                if storage == "real" else "complex64"),
+            "l2": "inputs larger than L2 (field %.0f MB > 129 MB L2)" % (6 * g.cells * vb / 1e6),
             "parallelism": "replicas"}
 
 
@@ -187,7 +198,7 @@ def run_ours(a):
     g, m, p, n_steps, plane = W.tight_focus_workload(N=a.size)
     dt = (m.R0 / g.c) / n_steps
     stream = torch.cuda.Stream(dev)
-    ctx = psatd.Context(g, m, dt, 32, stream=stream)
+    ctx = psatd.Context(g, m, dt, 32, stream=stream, real=(a.storage == "real"))
     out_dev = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
 
     def job(c, out):
@@ -212,56 +223,37 @@ def run_ours(a):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize(dev)
-    ctx.profile_enable(True)
-    n0 = ctx.launch_count
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(a.steps):
-        diag = job(ctx, out_dev)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    t_ms, prof, launches, diag = time_jobs(ctx, job, out_dev, a.steps, stream, dev)
     barrier()
-    launches = ctx.launch_count - n0
-    t_ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
     clk = clocks.stop()
     t_max = RP.max_over_ranks(t_ms, device=dev)
     value = RP.whole_job_rate(g.cells * n_steps * a.steps, world, t_max / 1e3)
-
-    # roofline of the dominant per-step kernel: algorithmic bytes = one read and one
-    # write of the six complex64 components (96 B per cell) per launch
     peak, peak_src = measured_peaks()
-    step_k = {k: v for k, v in prof.items() if k in STEP_KERNELS}
-    dom = max(step_k, key=lambda k: step_k[k][0])
-    dom_ms, dom_n = step_k[dom]
-    bytes_per_launch = 96 * g.cells
-    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
-    step_total = sum(v[0] for v in step_k.values())
+    roof, step_hbm = step_roofline(prof, g, a.storage, a.size, peak, peak_src)
     all_total = sum(v[0] for v in prof.values())
-    # whole-step HBM figure: 3 sweeps of 96 B per cell-step is the design floor
-    sweep_bytes = sum(96 * g.cells * v[1] for k, v in step_k.items())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(a.size),
+        "config": workload_config(a.size, a.storage),
         "focal_fields_per_s": world * a.steps / (t_max / 1e3),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
-                     if peak_src == "measured" else "fallback 6.8 TB/s",
-                     "traffic": NCU_TRAFFIC_BYTES.get((dom, a.size)), "bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": dom_ms / dom_n, "launches": dom_n},
+        "roofline": roof,
         "kernel_share": {k: round(v[0] / all_total, 4) for k, v in sorted(prof.items())},
-        "step_hbm": {"algorithmic_bytes_per_cell_step": sweep_bytes / (g.cells * n_steps * a.steps),
-                     "achieved_GBps": sweep_bytes / (step_total / 1e3) / 1e9,
-                     "frac_of_288B_design": (288 * g.cells * n_steps * a.steps) / (step_total / 1e3) / 1e9 / peak,
-                     "frac_of_96B_floor": (96 * g.cells * n_steps * a.steps) / (step_total / 1e3) / 1e9 / peak},
+        "step_hbm": step_hbm,
         "clocks": clk,
         "gpu_launches": launches,
         "diag_last": {"energy": diag["energy"], "max_div_E_rel": diag["max_div_E"] / max(diag["max_E_hat"], 1e-300)},
     }
+    # the other field storage, same job, fewer jobs (reported beside the headline)
+    other = "complex" if a.storage == "real" else "real"
+    with psatd.Context(g, m, dt, 32, stream=stream, real=(other == "real")) as c2:
+        job(c2, out_dev)
+        c2.synchronize()
+        k2 = max(1, min(a.steps, 2))
+        t2, prof2, _, _ = time_jobs(c2, job, out_dev, k2, stream, dev)
+        roof2, hbm2 = step_roofline(prof2, g, other, a.size, peak, peak_src)
+    line[other + "_storage"] = {"value": world * g.cells * n_steps * k2 / (t2 / 1e3), "unit": UNIT,
+                                "jobs": k2, "ms_per_job": t2 / k2, "roofline": roof2, "step_hbm": hbm2}
 
     if not a.no_e2e:
         line["e2e"] = e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world)
@@ -283,13 +275,63 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
 
 
+def time_jobs(ctx, job, out_dev, steps, stream, dev):
+    """Run `steps` jobs between CUDA events on the library stream with per-kernel
+    event timing on; returns (ms, per-kernel {name: (ms, launches)}, launches of
+    our kernels, last diagnostics)."""
+    import torch
+    ctx.profile_enable(True)
+    n0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    diag = None
+    for _ in range(steps):
+        diag = job(ctx, out_dev)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = ctx.launch_count - n0
+    t_ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    return t_ms, prof, launches, diag
+
+
+def step_roofline(prof, g, storage, size, peak, peak_src):
+    """Roofline of the dominant per-step kernel (algorithmic bytes = one read and
+    one write of the six stored components per cell per launch: 48 B real, 96 B
+    complex) and the whole-step HBM figure from every step kernel's launches."""
+    B = SWEEP_BYTES[storage]
+    step_k = {k: v for k, v in prof.items() if k in STEP_KERNELS}
+    dom = max(step_k, key=lambda k: step_k[k][0])
+    dom_ms, dom_n = step_k[dom]
+    bytes_per_launch = B * g.cells
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    # the packed-slot kernel touches the k_x = 0 pencils only: 6 x Ny x Nz complex64 read + write
+    per_launch = {k: (96 * g.Ny * g.Nz if k == "kspace_x0" else B * g.cells) for k in step_k}
+    sweep_bytes = sum(per_launch[k] * v[1] for k, v in step_k.items())
+    step_total = sum(v[0] for v in step_k.values())
+    n_full = sum(v[1] for k, v in step_k.items() if k != "kspace_x0")
+    n_st = step_k.get("kspace_z", (0.0, 0))[1] or max(n_full // 3, 1)     # one k-space launch per step
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_src == "measured" else "fallback 6.8 TB/s",
+            "traffic": NCU_TRAFFIC_BYTES.get((dom, size, storage)), "bytes_per_launch": bytes_per_launch,
+            "bytes_per_cell_per_launch": B, "avg_launch_ms": dom_ms / dom_n, "launches": dom_n}
+    hbm = {"algorithmic_bytes_per_cell_step": sweep_bytes / n_st / g.cells,
+           "achieved_GBps": sweep_bytes / (step_total / 1e3) / 1e9,
+           "frac_of_measured_peak": sweep_bytes / (step_total / 1e3) / 1e9 / peak,
+           "ms_per_psatd_step": step_total / n_st}
+    return roof, hbm
+
+
 def e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world):
     """The same job through the public API with host buffers: the initial six
     components come from pinned host memory (set_field), the focal plane and the
     diagnostics go back to the host, every step."""
     import torch
     ctx.init_pulse(p)
-    host_in = torch.empty((6, g.Nz, g.Ny, g.Nx), dtype=torch.complex64, pin_memory=True)
+    host_in = torch.empty((6, g.Nz, g.Ny, g.Nx), dtype=ctx.dtype, pin_memory=True)
     host_in.copy_(ctx.fields.cpu())
     host_out = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, pin_memory=True)
     import ctypes as C
@@ -364,6 +406,9 @@ def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_s
         res["one_shot_fp64"] = {"focal_fields_per_s": reps / (e0.elapsed_time(e1) / 1e3), "rel_l2_err_vs_fp64": 0.0}
     nref = float(np.linalg.norm(ref))
     res["stepped_fp32"] = {"rel_l2_err_vs_fp64": float(np.linalg.norm(stepped32.cpu().numpy() - ref) / nref)}
+    own = None
+    if ctx32.real:                       # the one-shot path works on complex storage
+        own = ctx32 = psatd.Context(g, m, dt, 32, stream=stream)
     out32 = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
     ctx32.focal_one_shot(p, T, *args, out=out32)
     ctx32.synchronize()
@@ -375,6 +420,8 @@ def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_s
     torch.cuda.synchronize(dev)
     res["one_shot_fp32"] = {"focal_fields_per_s": reps / (e0.elapsed_time(e1) / 1e3),
                             "rel_l2_err_vs_fp64": float(np.linalg.norm(out32.cpu().numpy() - ref) / nref)}
+    if own is not None:
+        own.close()
     res["stepped_fp64_estimate"] = {"focal_fields_per_s": 1e3 / (ms_step64 * n_steps),
                                     "note": "from the measured FP64 PSATD step time x %d steps" % n_steps}
     return res

@@ -105,10 +105,15 @@ template <typename T>
 cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
 
 // Half spectrum of real fields in the slot order of the real-field plane
-// kernels: per slot p < Nx/2, the wave number k_x and the octant index |m_x|.
+// kernels: per slot p < Nx/2 the wave number k_x, and the coefficient table
+// with its x index in slot order (column p = slot p, column Nx/2 = the x
+// Nyquist mode), (Nz/2+1) x (Ny/2+1) x (Nx/2+1) entries.
+// side: [6][Ny][Nz] complex, the z spectra of slot 0 handed from the k-space
+// pass to the slot-0 pass.
 template <typename T> struct HalfSlots {
     const T* k;
-    const int* ax;
+    const ModeCoef<T>* coef;
+    cplx<T>* side;
 };
 
 // Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
@@ -124,7 +129,8 @@ cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridG
 // Slot 0 of a real-field half spectrum (k_x = 0 packed with the x Nyquist
 // mode): unpack the two Hermitian spectra, apply the update, repack; all six
 // components, z transforms included.
-cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float>& tb, cudaStream_t s);
+cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float>& tb, const HalfSlots<float>& hs,
+                             cudaStream_t s);
 
 // Real-field plane transforms (FP32, 256 x 256 planes, in place): dir < 0 =
 // r2c along x + y, dir > 0 = inverse y + c2r.  Spectra are in slot order

@@ -29,15 +29,17 @@ namespace {
 //     touch only the thread's own positions and need no barrier.
 // HALF: the storage holds the half spectrum of real fields in the slot order of
 // the real-field plane kernels (x extent = Nx/2 slots): the slot's wave number
-// and octant index come from tables (kxs, slot_ax), modes on the y or z
+// comes from kxs and the coefficient table is in slot order along x (column =
+// slot, so neighbouring threads read neighbouring entries), modes on the y or z
 // Nyquist planes take the mean update that keeps the field real, and slot 0
-// (k_x = 0 packed with the x Nyquist mode) is left to kspace_x0_kernel.
+// (k_x = 0 packed with the x Nyquist mode) is left to kspace_x0_kernel: its
+// z spectra go to side[component][y][k_z] and the field keeps slot 0 unchanged.
 template <typename T, int N1, int N2, int W, bool SPECTRAL_OUT, bool HALF>
 __global__ void __launch_bounds__(W * N2)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
                   const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
                   const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err,
-                  bool project_b, const int* __restrict__ slot_ax, int coef_nx) {
+                  bool project_b, int coef_nx, cplx<T>* __restrict__ side) {
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
@@ -73,7 +75,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     cplx<T> twr[N1];
     static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
     const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
-    const int ax = HALF ? slot_ax[ix] : min(ix, Nx - ix), ay = min(y, Ny - y);
+    const int ax = HALF ? ix : min(ix, Nx - ix), ay = min(y, Ny - y);
     const T kx = kxs[ix], ky = kys[y];
     ModeCoef<T> mc[N1];
     T kzr[N1];
@@ -135,6 +137,17 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
             cplx<T>* sl = own + (q0 + b) * SLOT;
             static_for<0, N1>([&](auto rc) { sl[decltype(rc)::value * RP] = v[b][decltype(rc)::value]; });
         });
+    }
+
+    if constexpr (HALF) {
+        if (ix == 0) {
+            static_for<0, N1>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                const int iz = (j + N2 * (r / N2)) + N1 * (r % N2);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) side[((size_t)q * Ny + y) * Nz + iz] = own[q * SLOT + r * RP];
+            });
+        }
     }
 
     // per-mode update on the thread's own modes (no barrier needed)
@@ -232,7 +245,8 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     const int nx = half ? g.Nx / 2 : g.Nx;             // complex elements per stored row
     const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W));
     k<<<blocks, W * N2, smem, s>>>(map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
-                                   tb.coef, err, project_b, half ? half->ax : nullptr, g.Nx / 2 + 1);
+                                   half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
+                                   half ? half->side : nullptr);
     return cudaGetLastError();
 }
 

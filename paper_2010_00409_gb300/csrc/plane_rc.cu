@@ -29,7 +29,11 @@
 // cluster barrier, inverse stage A per row, stores.
 //
 // Shared memory: one 32 KB tile per block, swizzled (column ^ (row & 15)) so
-// that every access pattern above runs at two wavefronts per warp.
+// that every access pattern above runs at two wavefronts per warp.  Remote
+// stores are cheapest when the 32 lanes of one store write one contiguous
+// block: in the inverse the tile receives the rows as [k1][j][row ^ j] (256
+// contiguous bytes per store), a scattered [row][column] target cost twice the
+// kernel's time.
 #include <cooperative_groups.h>
 
 #include "fft_reg.cuh"
@@ -45,9 +49,8 @@ constexpr int kRcC = 8;               // blocks per plane (cluster size)
 constexpr int kM = 128;               // complex elements per row
 constexpr int kNy = 256;
 
-// tile [256][16] and, in the inverse, [32][128]
+// tile [256][16]
 __device__ __forceinline__ int sw16(int row, int col) { return row * 16 + (col ^ (row & 15)); }
-__device__ __forceinline__ int sw128(int row, int col) { return row * 128 + (col ^ (row & 15)); }
 
 constexpr int owner_of(int k1) { return (k1 == 0 || k1 == 8) ? 0 : (k1 < 8 ? k1 : 16 - k1); }
 constexpr int half_of(int k1) { return (k1 == 0) ? 0 : (k1 == 8 ? 1 : (k1 < 8 ? 0 : 1)); }
@@ -165,7 +168,7 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
 __global__ void __launch_bounds__(kRcThreads)
 plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tile = reinterpret_cast<float2*>(smem_raw);
+    float2* tile = reinterpret_cast<float2*>(smem_raw);   // [256][16] this block's columns, then [16][8][32] rows
 
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
@@ -229,13 +232,15 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
             });
         });
         cluster.barrier_wait();
+        // row y goes to block y / 32; element (k1, j) of local row yl at k1 * 256 + j * 32 + (yl ^ j):
+        // the warp's 32 rows fill one contiguous 256-byte block per store
         float2* dst = cluster.map_shared_rank(tile, y >> 5);
         const int yl = y & 31;
         static_for<0, 2>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
             static_for<0, 8>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
-                dst[sw128(yl, k1s[s] * 8 + j)] = z[s][j];
+                dst[k1s[s] * 256 + j * 32 + (yl ^ j)] = z[s][j];
             });
         });
     }
@@ -246,7 +251,7 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
         const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
         const int yl = w + 8 * g;
         float2 v[16];
-        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[sw128(yl, decltype(kc)::value * 8 + j)]; });
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[decltype(kc)::value * 256 + j * 32 + (yl ^ j)]; });
         reg_dft<float, +1, 16>(v);                     // v[n1] = z[j + 8 n1]
         float2* p = plane + (size_t)(32 * r + yl) * kM;
         static_for<0, 16>([&](auto nc) { p[j + 8 * decltype(nc)::value] = v[decltype(nc)::value]; });

@@ -85,7 +85,8 @@ struct psatd_ctx {
     bool own_fields = false;
     bool real_fields = false;           // real float32 storage (PSATD_FLAG_REAL_FIELDS)
     DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
-    DevBuf slot_k, slot_ax;             // real fields: k_x and |m_x| per half-spectrum slot
+    DevBuf slot_k, slot_coef;           // real fields: k_x per slot, coefficient table in slot order
+    DevBuf slot0_side;                  // real fields: z spectra of slot 0 between the k-space passes
 
     // tables (device)
     DevBuf tw[3], k[3], coef;
@@ -214,8 +215,10 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
 }
 
 // (C/Ntot, S/Ntot, 1/|k|) per |m| octant, float64 then rounded once.
+// slot_order: column p < Nx/2 holds the x mode of half-spectrum slot p (real
+// fields), column Nx/2 the x Nyquist mode.
 template <typename T>
-psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr) {
+psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr, bool slot_order = false) {
     DevBuf& buf = dst ? *dst : c->coef;
     const psatd_grid& g = c->grid;
     const int hx = g.Nx / 2 + 1, hy = g.Ny / 2 + 1, hz = g.Nz / 2 + 1;
@@ -226,7 +229,8 @@ psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr) {
         for (int ay = 0; ay < hy; ++ay) {
             const double ky = kTwoPi * ay / (g.Ny * g.dy);
             for (int ax = 0; ax < hx; ++ax) {
-                const double kx = kTwoPi * ax / (g.Nx * g.dx);
+                const int mx = (slot_order && ax < g.Nx / 2) ? plane_rc_slot_mode(ax) : ax;
+                const double kx = kTwoPi * mx / (g.Nx * g.dx);
                 const double km = std::sqrt(kx * kx + ky * ky + kz * kz);
                 ModeCoef<T> m;
                 m.C = (T)(std::cos(g.c * km * dt) / ntot);
@@ -245,7 +249,9 @@ psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr) {
 }
 
 psatd_status set_coef(psatd_ctx* c, double dt) {
-    return c->prec == 64 ? upload_coef<double>(c, dt) : upload_coef<float>(c, dt);
+    psatd_status st = c->prec == 64 ? upload_coef<double>(c, dt) : upload_coef<float>(c, dt);
+    if (st == PSATD_OK && c->real_fields) st = upload_coef<float>(c, dt, &c->slot_coef, true);
+    return st;
 }
 
 psatd_batch* capturing(const psatd_ctx* c);
@@ -475,7 +481,9 @@ cudaError_t spectral_pass_real(psatd_ctx* c) {
     });
     if (e != cudaSuccess) return e;
     if (!ensure_field_map(c)) return cudaErrorNotSupported;
-    const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p), static_cast<const int*>(c->slot_ax.p)};
+    const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p),
+                              static_cast<const ModeCoef<float>*>(c->slot_coef.p),
+                              static_cast<float2*>(c->slot0_side.p)};
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
         ++c->launches;
         return launch_kspace_tma<float>(c->field_map, reinterpret_cast<cplx<float>*>(f), g, tb, c->dev_err, c->stream,
@@ -484,7 +492,7 @@ cudaError_t spectral_pass_real(psatd_ctx* c) {
     if (e != cudaSuccess) return e;
     e = timed(c, PSATD_KERNEL_KSPACE_X0, [&] {
         ++c->launches;
-        return launch_kspace_x0(reinterpret_cast<float2*>(f), g, tb, c->stream);
+        return launch_kspace_x0(reinterpret_cast<float2*>(f), g, tb, hs, c->stream);
     });
     if (e != cudaSuccess) return e;
     return timed(c, PSATD_KERNEL_PLANE_XY, [&] {
@@ -525,16 +533,11 @@ psatd_status ensure_scratch(psatd_ctx* c, bool widen) {
 psatd_status upload_slot_tables(psatd_ctx* c) {
     const int nh = c->grid.Nx / 2;
     std::vector<float> k(nh);
-    std::vector<int> ax(nh);
-    for (int p = 0; p < nh; ++p) {
-        const int m = plane_rc_slot_mode(p);
-        ax[p] = m;
-        k[p] = (float)(kTwoPi * (double)m / (c->grid.Nx * c->grid.dx));
-    }
+    for (int p = 0; p < nh; ++p)
+        k[p] = (float)(kTwoPi * (double)plane_rc_slot_mode(p) / (c->grid.Nx * c->grid.dx));
     CK(c, ensure_buf(c->slot_k, nh * sizeof(float)));
-    CK(c, ensure_buf(c->slot_ax, nh * sizeof(int)));
     CK(c, cudaMemcpy(c->slot_k.p, k.data(), nh * sizeof(float), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->slot_ax.p, ax.data(), nh * sizeof(int), cudaMemcpyHostToDevice));
+    CK(c, ensure_buf(c->slot0_side, (size_t)6 * c->grid.Ny * c->grid.Nz * sizeof(float2)));
     return PSATD_OK;
 }
 
@@ -682,7 +685,7 @@ void psatd_destroy(psatd_ctx* c) {
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
     free_buf(c->coef_T);
-    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_ax);
+    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->slot0_side);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
