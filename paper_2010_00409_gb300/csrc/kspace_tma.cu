@@ -3,10 +3,11 @@
 // (one per field component, box = W x-columns x 1 y x Nz z, 64 contiguous bytes
 // per row) into the six shared-memory slots, all completing on one mbarrier.
 // The whole tile (6 * Nz * W complex values) is then in flight at once, while
-// the other resident block computes.  Per component: forward z transform in
+// the other resident block computes.  The block's threads form two groups; each
+// group transforms three components.  Per component: forward z transform in
 // registers (the slot doubles as the exchange buffer), spectrum back to the
-// slot; the per-mode update over all six slots; inverse z transforms stored
-// straight from registers to the field.
+// slot; the per-mode update over all six slots (modes split between the
+// groups); inverse z transforms stored straight from registers to the field.
 //
 // The wait on the copies is bounded: past the limit the block sets an error bit
 // in the context's device error word and returns without touching the field.
@@ -34,8 +35,8 @@ namespace {
 // Nyquist planes take the mean update that keeps the field real, and slot 0
 // (k_x = 0 packed with the x Nyquist mode) is left to kspace_x0_kernel: its
 // z spectra go to side[component][y][k_z] and the field keeps slot 0 unchanged.
-template <typename T, int N1, int N2, int W, bool SPECTRAL_OUT, bool HALF>
-__global__ void __launch_bounds__(W * N2)
+template <typename T, int N1, int N2, int W, int G, bool SPECTRAL_OUT, bool HALF>
+__global__ void __launch_bounds__(W * N2 * G)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
                   const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
                   const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err,
@@ -43,15 +44,20 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
-    constexpr int NB = sizeof(T) == 4 ? 2 : 1;                 // components per exchange round
+    constexpr int NT = W * N2;                                  // threads of one group
+    constexpr int NC = 6 / G;                                   // components transformed by one group
+    constexpr int NB = (G == 1 && sizeof(T) == 4) ? 2 : 1;      // components per exchange round
+    constexpr int NM = N1 / G;                                  // modes updated per thread
     constexpr uint32_t kBytes = 6u * Nz * W * sizeof(cplx<T>);
     static_assert(kBytes < (1u << 20), "mbarrier transaction count is 20 bits");
+    static_assert(NC % NB == 0 && N1 % G == 0, "group split");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cplx<T>* spec = reinterpret_cast<cplx<T>*>(smem_raw);      // [6][N1][RP]
     __shared__ __align__(8) uint64_t bar;
     __shared__ int failed;
 
-    const int c = threadIdx.x % W, j = threadIdx.x / W;
+    const int t = threadIdx.x % NT, h = threadIdx.x / NT;       // group h: components NC h .. NC h + NC - 1
+    const int c = t % W, j = t / W;
     const size_t plane = (size_t)Nx * Ny;
     const size_t cstride = plane * Nz;
     const int ntile = Nx / W;
@@ -71,23 +77,22 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     }
 
     // while the copies fly: outer twiddles W_N^{j k1} (the inverse uses their
-    // conjugates with k1 = j) and the per-mode coefficients of this thread's modes
+    // conjugates with k1 = j) and the per-mode coefficients of this thread's
+    // modes (registers r = h NM .. h NM + NM - 1 of position (c, j))
     cplx<T> twr[N1];
     static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
     const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
     const int ax = HALF ? ix : min(ix, Nx - ix), ay = min(y, Ny - y);
     const T kx = kxs[ix], ky = kys[y];
-    ModeCoef<T> mc[N1];
-    T kzr[N1];
-    static_for<0, N1 / N2>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        static_for<0, N2>([&](auto kc) {
-            constexpr int k2 = decltype(kc)::value;
-            const int iz = (j + N2 * q) + N1 * k2;
-            const int az = min(iz, Nz - iz);
-            mc[q * N2 + k2] = coef[((size_t)az * Nyh + ay) * Nxh + ax];
-            kzr[q * N2 + k2] = kzs[iz];
-        });
+    ModeCoef<T> mc[NM];
+    T kzr[NM];
+    static_for<0, NM>([&](auto mcix) {
+        constexpr int m = decltype(mcix)::value;
+        const int r = h * NM + m;
+        const int iz = (j + N2 * (r / N2)) + N1 * (r % N2);
+        const int az = min(iz, Nz - iz);
+        mc[m] = coef[((size_t)az * Nyh + ay) * Nxh + ax];
+        kzr[m] = kzs[iz];
     });
 
     if (threadIdx.x == 0) {
@@ -101,12 +106,12 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     __syncthreads();
     if (failed) return;
 
-    cplx<T>* own = spec + j * W + c;                           // (row r, this thread) at own[r * RP]
+    cplx<T>* own = spec + j * W + c;                           // (row r, position (c, j)) at own[r * RP]
     cplx<T> v[NB][N1];
 
-    // forward z transforms, NB components per exchange round
+    // forward z transforms of this group's components, NB per exchange round
 #pragma unroll 1
-    for (int q0 = 0; q0 < 6; q0 += NB) {
+    for (int q0 = NC * h; q0 < NC * h + NC; q0 += NB) {
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             cplx<T>* sl = own + (q0 + b) * SLOT;
@@ -138,11 +143,12 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
             static_for<0, N1>([&](auto rc) { sl[decltype(rc)::value * RP] = v[b][decltype(rc)::value]; });
         });
     }
+    if constexpr (G > 1) __syncthreads();                      // the update reads the other group's components
 
     if constexpr (HALF) {
         if (ix == 0) {
-            static_for<0, N1>([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
+            static_for<0, NM>([&](auto mcix) {
+                const int r = h * NM + decltype(mcix)::value;
                 const int iz = (j + N2 * (r / N2)) + N1 * (r % N2);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) side[((size_t)q * Ny + y) * Nz + iz] = own[q * SLOT + r * RP];
@@ -150,29 +156,31 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         }
     }
 
-    // per-mode update on the thread's own modes (no barrier needed)
-    static_for<0, N1>([&](auto rc) {
-        constexpr int r = decltype(rc)::value;
+    // per-mode update on this thread's modes of position (c, j)
+    static_for<0, NM>([&](auto mcix) {
+        constexpr int m = decltype(mcix)::value;
+        const int r = h * NM + m;
         cplx<T>* o = own + r * RP;
         cplx<T> Ex = o[0], Ey = o[SLOT], Ez = o[2 * SLOT];
         cplx<T> Bx = o[3 * SLOT], By = o[4 * SLOT], Bz = o[5 * SLOT];
-        const ModeCoef<T> m = mc[r];
+        const ModeCoef<T> mm = mc[m];
         if constexpr (HALF) {
-            constexpr int q = r / N2, k2 = r % N2;
-            const bool fz = ((j + N2 * q) + N1 * k2) == Nz / 2;
-            rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, false,
-                                y == Ny / 2, fz, m.C, m.S);
+            const bool fz = ((j + N2 * (r / N2)) + N1 * (r % N2)) == Nz / 2;
+            rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, false,
+                                y == Ny / 2, fz, mm.C, mm.S);
         } else {
-            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzr[r] * m.kinv, m.C, m.S, project_b);
+            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, mm.C, mm.S,
+                           project_b);
         }
         o[0] = Ex; o[SLOT] = Ey; o[2 * SLOT] = Ez;
         o[3 * SLOT] = Bx; o[4 * SLOT] = By; o[5 * SLOT] = Bz;
     });
+    if constexpr (G > 1) __syncthreads();                      // the inverse reads the other group's modes
 
     cplx<T>* base = data + (size_t)y * Nx + ix;
     if constexpr (SPECTRAL_OUT) {
         // store the updated spectrum in natural kz order (one-shot focal path)
-        for (int q = 0; q < 6; ++q) {
+        for (int q = NC * h; q < NC * h + NC; ++q) {
             const cplx<T>* sl = own + q * SLOT;
             cplx<T>* p = base + q * cstride;
             static_for<0, N1 / N2>([&](auto qc) {
@@ -186,9 +194,9 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         return;
     }
 
-    // inverse z transforms, NB components per exchange round
+    // inverse z transforms of this group's components, NB per exchange round
 #pragma unroll 1
-    for (int q0 = 0; q0 < 6; q0 += NB) {
+    for (int q0 = NC * h; q0 < NC * h + NC; q0 += NB) {
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const cplx<T>* sl = own + (q0 + b) * SLOT;
@@ -233,20 +241,24 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     }
 }
 
+// Two thread groups per block (each transforms three components; the update
+// splits the tile's modes between them): 256 threads at ~128 registers, twice
+// the resident warps of one group per block at the same shared memory.
 template <typename T, int N1, int N2, int W>
 cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
                               int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
+    constexpr int G = 2;
     const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
-    auto k = half ? kspace_tma_kernel<T, N1, N2, W, false, true>
-                  : (spectral_out ? kspace_tma_kernel<T, N1, N2, W, true, false>
-                                  : kspace_tma_kernel<T, N1, N2, W, false, false>);
+    auto k = half ? kspace_tma_kernel<T, N1, N2, W, G, false, true>
+                  : (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, false>
+                                  : kspace_tma_kernel<T, N1, N2, W, G, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nx = half ? g.Nx / 2 : g.Nx;             // complex elements per stored row
     const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W));
-    k<<<blocks, W * N2, smem, s>>>(map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
-                                   half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
-                                   half ? half->side : nullptr);
+    k<<<blocks, W * N2 * G, smem, s>>>(map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
+                                       half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
+                                       half ? half->side : nullptr);
     return cudaGetLastError();
 }
 

@@ -4,14 +4,14 @@
 // packed value P = S0 + i SN of the k_x = 0 spectrum S0 and the x Nyquist
 // spectrum SN of the real fields (each Hermitian in (k_y, k_z)).  The k-space
 // pass leaves the z spectra of slot 0 in side[component][y][k_z]; one block
-// takes the pencils at y and at its mirror Ny - y for all six components,
+// takes the pencil at y for all six components, reads its mirror at Ny - y,
 // unpacks
 //   S0(k) = (P(k) + conj P(-k)) / 2,   SN(k) = (P(k) - conj P(-k)) / (2i),
 // applies the update of Sec. 2.1 (Eq. 3-4) to both, with the mean over the
 // mirrored Nyquist wave vectors that keeps the fields real (k_x = -pi/dx is a
 // Nyquist component of SN), repacks P' = S0' + i SN', transforms back along z
-// and stores slot 0.  The data is 1/128 of the field, so the inverse transform
-// is the generic shared-memory Stockham one over the 12 pencils.
+// and stores slot 0 at y.  The data is 1/128 of the field, so the inverse
+// transform is the generic shared-memory Stockham one over the 6 pencils.
 #include "fft_core.cuh"
 #include "fft_reg.cuh"
 
@@ -27,25 +27,20 @@ kspace_x0_kernel(float2* __restrict__ data, const float2* __restrict__ side, int
                  float kx_nyq, const float* __restrict__ kys, const float* __restrict__ kzs,
                  const ModeCoef<float>* __restrict__ coef, int Nxh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* a = reinterpret_cast<float2*>(smem_raw);      // [12][Nz]: pencil (s, q) at (s * 6 + q) * Nz
-    float2* b = a + 12 * Nz;
-    const int ky = blockIdx.x;                            // 0 .. Ny/2
-    const int ys[2] = {ky, (Ny - ky) % Ny};
-    const bool single = ys[0] == ys[1];
+    float2* a = reinterpret_cast<float2*>(smem_raw);      // [6][Nz]: component q at q * Nz
+    float2* b = a + 6 * Nz;
+    const int y = blockIdx.x, ym = (Ny - y) % Ny;          // this pencil and its mirror
     const size_t plane = (size_t)Nh * Ny, cstride = plane * Nz;
 
     const int Nyh = Ny / 2 + 1, ax_nyq = Nxh - 1;
-    for (int e = threadIdx.x; e < 2 * Nz; e += blockDim.x) {
-        const int s = e / Nz, kz = e % Nz;
-        const int ps = single ? s : 1 - s;
+    for (int kz = threadIdx.x; kz < Nz; kz += blockDim.x) {
         const int kzm = (Nz - kz) % Nz;
-        const int y = ys[s];
         const int ay = min(y, Ny - y), az = min(kz, Nz - kz);
         const bool fy = (2 * y == Ny), fz = (2 * kz == Nz);
         float2 S0[6], SN[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            const float2 P1 = side[((size_t)q * Ny + ys[s]) * Nz + kz], P2 = side[((size_t)q * Ny + ys[ps]) * Nz + kzm];
+            const float2 P1 = side[((size_t)q * Ny + y) * Nz + kz], P2 = side[((size_t)q * Ny + ym) * Nz + kzm];
             S0[q] = make_float2(0.5f * (P1.x + P2.x), 0.5f * (P1.y - P2.y));
             SN[q] = make_float2(0.5f * (P1.y + P2.y), -0.5f * (P1.x - P2.x));
         }
@@ -57,14 +52,13 @@ kspace_x0_kernel(float2* __restrict__ data, const float2* __restrict__ side, int
         rotate_mode_mean<float>(SN[0], SN[1], SN[2], SN[3], SN[4], SN[5], kx_nyq * mn.kinv, kyv * mn.kinv,
                                 kzv * mn.kinv, true, fy, fz, mn.C, mn.S);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) a[(s * 6 + q) * Nz + kz] = make_float2(S0[q].x - SN[q].y, S0[q].y + SN[q].x);
+        for (int q = 0; q < 6; ++q) a[q * Nz + kz] = make_float2(S0[q].x - SN[q].y, S0[q].y + SN[q].x);
     }
     __syncthreads();
-    float2* g = fft_tile<float, +1>(a, b, pz, 12, Nz, twz);
-    const int nstore = (single ? 6 : 12) * Nz;
-    for (int e = threadIdx.x; e < nstore; e += blockDim.x) {
-        const int z = e % Nz, pq = e / Nz, s = pq / 6, q = pq % 6;
-        data[q * cstride + (size_t)z * plane + (size_t)ys[s] * Nh] = g[e];
+    float2* g = fft_tile<float, +1>(a, b, pz, 6, Nz, twz);
+    for (int e = threadIdx.x; e < 6 * Nz; e += blockDim.x) {
+        const int z = e % Nz, q = e / Nz;
+        data[q * cstride + (size_t)z * plane + (size_t)y * Nh] = g[e];
     }
 }
 
@@ -87,10 +81,10 @@ unsigned elementwise_blocks(size_t n) {
 
 cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float>& tb, const HalfSlots<float>& hs,
                              cudaStream_t s) {
-    const size_t smem = (size_t)2 * 12 * g.Nz * sizeof(float2);
+    const size_t smem = (size_t)2 * 6 * g.Nz * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(kspace_x0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kspace_x0_kernel<<<g.Ny / 2 + 1, kX0Threads, smem, s>>>(data, hs.side, g.Nx / 2, g.Ny, g.Nz, tb.plan[2], tb.tw[2],
+    kspace_x0_kernel<<<g.Ny, kX0Threads, smem, s>>>(data, hs.side, g.Nx / 2, g.Ny, g.Nz, tb.plan[2], tb.tw[2],
                                                             (float)(-3.14159265358979323846 / g.dx), tb.k[1], tb.k[2],
                                                             hs.coef, g.Nx / 2 + 1);
     return cudaGetLastError();
