@@ -34,6 +34,22 @@ template <typename V> __host__ __device__ __forceinline__ V cmul_si(V a, int s) 
     V r; if (s > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r;
 }
 
+// |a|^2 + |b|^2 + |c|^2 of one cell's three components, formed in the storage
+// precision (float32 storage: float32 products and sums, relative error ~1e-7)
+// and returned as float64 for the accumulation over cells.  The diagnostics and
+// the allocation-free energy kernel share it, so their results differ only in
+// the order of the float64 sums.
+template <typename T>
+__device__ __forceinline__ double cell_energy3(cplx<T> a, cplx<T> b, cplx<T> c) {
+    T s = a.x * a.x;
+    s = fma(a.y, a.y, s);
+    s = fma(b.x, b.x, s);
+    s = fma(b.y, b.y, s);
+    s = fma(c.x, c.x, s);
+    s = fma(c.y, c.y, s);
+    return (double)s;
+}
+
 // ---------------------------------------------------------------------------
 // 1D plan of one axis: N = prod(radix[0..npass)), radices in {2,3,4,5,8}
 // ---------------------------------------------------------------------------

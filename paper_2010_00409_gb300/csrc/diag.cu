@@ -2,7 +2,9 @@
 // divergence max_k |k^ . F(k)| of an already-transformed 3-component field
 // (Poisson's equation k^ . E^ = 0 is the constraint of Sec. 2.1).  Block
 // partials are written to a scratch array and reduced by one block in a fixed
-// order, so results are deterministic; accumulation is float64.
+// order, so results are deterministic.  Per-cell and per-mode values are formed
+// in the storage precision (float32 storage: float32 arithmetic, relative error
+// ~1e-7, far below the float32 solver's own); sums over cells are float64.
 #include "common.cuh"
 
 namespace psatd {
@@ -42,12 +44,8 @@ energy_kernel(const cplx<T>* __restrict__ f, size_t n, double* __restrict__ part
     __shared__ double sh[kThreads / 32];
     double eE = 0.0, eB = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        for (int c = 0; c < 3; ++c) {
-            const cplx<T> v = f[c * n + i];
-            eE += (double)v.x * v.x + (double)v.y * v.y;
-            const cplx<T> w = f[(3 + c) * n + i];
-            eB += (double)w.x * w.x + (double)w.y * w.y;
-        }
+        eE += cell_energy3<T>(f[i], f[n + i], f[2 * n + i]);
+        eB += cell_energy3<T>(f[3 * n + i], f[4 * n + i], f[5 * n + i]);
     }
     const double sE = block_sum(eE, sh);
     const double sB = block_sum(eB, sh);
@@ -61,23 +59,25 @@ divergence_kernel(const cplx<T>* __restrict__ F, GridGeom g, const T* __restrict
                   const T* __restrict__ ky, const T* __restrict__ kz, double* __restrict__ partial) {
     __shared__ double sh[kThreads / 32];
     const size_t n = (size_t)g.Nx * g.Ny * g.Nz;
-    double md = 0.0, mf = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % g.Nx);
-        const size_t r = i / g.Nx;
-        const int iy = (int)(r % g.Ny), iz = (int)(r / g.Ny);
-        const double a = kx[ix], b = ky[iy], c = kz[iz];
-        const double km = sqrt(a * a + b * b + c * c);
-        const double inv = km > 0.0 ? 1.0 / km : 0.0;
-        const cplx<T> X = F[i], Y = F[n + i], Z = F[2 * n + i];
-        const double dr = (a * X.x + b * Y.x + c * Z.x) * inv;
-        const double di = (a * X.y + b * Y.y + c * Z.y) * inv;
-        md = fmax(md, sqrt(dr * dr + di * di));
-        mf = fmax(mf, sqrt((double)X.x * X.x + (double)X.y * X.y + (double)Y.x * Y.x +
-                           (double)Y.y * Y.y + (double)Z.x * Z.x + (double)Z.y * Z.y));
+    const int rows = g.Ny * g.Nz;
+    T md2 = 0, mf2 = 0;                                // squared maxima
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int iy = row % g.Ny, iz = row / g.Ny;
+        const T b = ky[iy], c = kz[iz];
+        const size_t base = (size_t)row * g.Nx;
+        for (int ix = threadIdx.x; ix < g.Nx; ix += blockDim.x) {
+            const T a = kx[ix];
+            const T k2 = a * a + b * b + c * c;
+            const size_t i = base + ix;
+            const cplx<T> X = F[i], Y = F[n + i], Z = F[2 * n + i];
+            const T dr = a * X.x + b * Y.x + c * Z.x;
+            const T di = a * X.y + b * Y.y + c * Z.y;
+            if (k2 > T(0)) md2 = max(md2, (dr * dr + di * di) / k2);
+            mf2 = max(mf2, (T)cell_energy3<T>(X, Y, Z));
+        }
     }
-    const double bd = block_max(md, sh);
-    const double bf = block_max(mf, sh);
+    const double bd = block_max(sqrt((double)md2), sh);
+    const double bf = block_max(sqrt((double)mf2), sh);
     if (threadIdx.x == 0) { partial[2 * blockIdx.x] = bd; partial[2 * blockIdx.x + 1] = bf; }
 }
 

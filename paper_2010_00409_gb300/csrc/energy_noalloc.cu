@@ -51,12 +51,8 @@ energy_partials_kernel(const cplx<T>* __restrict__ f, long long n, double* __res
     const long long end = min(begin + kCellsPerPartial, n);
     double eE = 0.0, eB = 0.0;
     for (long long i = begin + threadIdx.x; i < end; i += kThreads) {
-        for (int c = 0; c < 3; ++c) {
-            const cplx<T> a = f[c * n + i];
-            const cplx<T> b = f[(3 + c) * n + i];
-            eE += (double)a.x * a.x + (double)a.y * a.y;
-            eB += (double)b.x * b.x + (double)b.y * b.y;
-        }
+        eE += cell_energy3<T>(f[i], f[n + i], f[2 * n + i]);
+        eB += cell_energy3<T>(f[3 * n + i], f[4 * n + i], f[5 * n + i]);
     }
     eE = warp_sum(eE);
     eB = warp_sum(eB);

@@ -113,6 +113,7 @@ struct psatd_ctx {
     DevBuf coef_T;
     double coef_T_step = 0.0;
     bool coef_T_ok = false;
+    DevBuf coef_proj;                   // C = 1/Ntot, S = 0: the projection through the TMA kernel
     bool holds_spectrum = false;
     std::string err = "no error";
 
@@ -216,9 +217,12 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
 
 // (C/Ntot, S/Ntot, 1/|k|) per |m| octant, float64 then rounded once.
 // slot_order: column p < Nx/2 holds the x mode of half-spectrum slot p (real
-// fields), column Nx/2 the x Nyquist mode.
+// fields), column Nx/2 the x Nyquist mode.  projection: C = 1/Ntot, S = 0 (with
+// the B projection of the k-space kernel this is the one-time transverse
+// projection).
 template <typename T>
-psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr, bool slot_order = false) {
+psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr, bool slot_order = false,
+                         bool projection = false) {
     DevBuf& buf = dst ? *dst : c->coef;
     const psatd_grid& g = c->grid;
     const int hx = g.Nx / 2 + 1, hy = g.Ny / 2 + 1, hz = g.Nz / 2 + 1;
@@ -233,8 +237,8 @@ psatd_status upload_coef(psatd_ctx* c, double dt, DevBuf* dst = nullptr, bool sl
                 const double kx = kTwoPi * mx / (g.Nx * g.dx);
                 const double km = std::sqrt(kx * kx + ky * ky + kz * kz);
                 ModeCoef<T> m;
-                m.C = (T)(std::cos(g.c * km * dt) / ntot);
-                m.S = (T)(std::sin(g.c * km * dt) / ntot);
+                m.C = (T)((projection ? 1.0 : std::cos(g.c * km * dt)) / ntot);
+                m.S = (T)(projection ? 0.0 : std::sin(g.c * km * dt) / ntot);
                 m.kinv = (T)(km > 0 ? 1.0 / km : 0.0);
                 m.pad = (T)0;
                 tab[((size_t)az * hy + ay) * hx + ax] = m;
@@ -448,6 +452,20 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
         if (mode == KS_ROTATE && c->kernel_path == PSATD_PATH_AUTO && ensure_field_map(c)) {
             cudaError_t r = launch_kspace_tma<T>(c->field_map, f, g, tb, c->dev_err, c->stream);
+            if (r != cudaErrorNotSupported) {
+                ++c->launches;
+                return r;
+            }
+        }
+        // (the table is built on first use, outside graph capture; a capture before
+        // that takes the generic projection below)
+        if (mode == KS_PROJECT && c->kernel_path == PSATD_PATH_AUTO && (c->coef_proj.p || !capturing(c)) &&
+            ensure_field_map(c)) {
+            if (!c->coef_proj.p && upload_coef<T>(c, 0.0, &c->coef_proj, false, true) != PSATD_OK)
+                return cudaErrorMemoryAllocation;
+            Tables<T> tp = tb;
+            tp.coef = static_cast<const ModeCoef<T>*>(c->coef_proj.p);
+            cudaError_t r = launch_kspace_tma<T>(c->field_map, f, g, tp, c->dev_err, c->stream, false, true);
             if (r != cudaErrorNotSupported) {
                 ++c->launches;
                 return r;
@@ -685,6 +703,7 @@ void psatd_destroy(psatd_ctx* c) {
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
     free_buf(c->coef_T);
+    free_buf(c->coef_proj);
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->slot0_side);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);

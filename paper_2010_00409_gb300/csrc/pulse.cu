@@ -3,8 +3,12 @@
 // Each node (x~_i, y_j, z_l) of the layer is the image under the mapping T of
 // Eq. 13 of the physical points x~_i + m D, y_j, z_l; its field is the sum of the
 // pulse over those replicas m (replicas that do not overlap contribute at most
-// one nonzero term).  Coordinates, angles and the pulse are evaluated in float64
-// and rounded once to the storage precision.
+// one nonzero term).  float64 storage: coordinates, angles and the pulse are
+// evaluated in float64 and rounded once.  float32 storage: the distance R, the
+// offset zeta = R - R0 and the carrier phase (reduced to [-pi, pi]) in float64 —
+// the phase 2 pi zeta / lambda needs ~1e-7 rad at R ~ 20 lambda — and the rest
+// (angle, windows, polarisation vectors) in float32, adding ~1e-7 relative error
+// to the rounding to float32 (float64 arithmetic is the scarce unit on GB300).
 #include "common.cuh"
 
 namespace psatd {
@@ -60,6 +64,57 @@ __device__ __forceinline__ void pol_vectors(double X, double Y, double Z, double
     s1[0] = a0 * i1; s1[1] = a1 * i1; s1[2] = a2 * i1;
 }
 
+// float32-storage variants of u_ts_flat, pulse_u and pol_vectors
+__device__ __forceinline__ float u_ts_flat_f(float a, float th, float eps) {
+    if (a <= th - 0.5f * eps) return 1.f;
+    if (a <= th + 0.5f * eps) {
+        const float c = cosf((float)kPi * (a - th + 0.5f * eps) / (2.f * eps));
+        return c * c;
+    }
+    return 0.f;
+}
+
+__device__ __forceinline__ float pulse_u_f(double X, double Y, double Z, const PulseParams& p, const ShellGeom& sh,
+                                           double phase) {
+    // cheap rejection of points well outside the shell (float32 R^2, margin 1e-4)
+    const float xf = (float)X, yf = (float)Y, zf2 = (float)Z;
+    const float r2 = xf * xf + yf * yf + zf2 * zf2;
+    const float lo = (float)(sh.R0 - 0.5 * sh.L), hi = (float)(sh.R0 + 0.5 * sh.L);
+    if (r2 < lo * lo * 0.9999f || r2 > hi * hi * 1.0001f) return 0.f;
+    const double R = sqrt(X * X + Y * Y + Z * Z);
+    if (!(R > 0.0)) return 0.f;
+    const double zeta = R - sh.R0;
+    if (zeta < -0.5 * sh.L || zeta > 0.5 * sh.L) return 0.f;
+    const float alpha = atan2f(sqrtf((float)(Y * Y + Z * Z)), (float)(-X));
+    const double arg = 2.0 * kPi * zeta / p.lambda + phase;
+    const float carrier = sinf((float)(arg - 2.0 * kPi * rint(arg / (2.0 * kPi))));
+    const float zf = (float)zeta;
+    if (p.kind == 0) {
+        const float uts = u_ts_flat_f(alpha, (float)p.theta, (float)p.eps);
+        if (uts == 0.f) return 0.f;
+        const float cl = cosf((float)kPi * zf / (float)sh.L);
+        return (float)(p.amp / R) * carrier * cl * cl * uts;
+    }
+    float uts = u_ts_flat_f(alpha, (float)(2.0 * p.theta), (float)p.eps);
+    if (uts == 0.f) return 0.f;
+    const float th = (float)p.theta;
+    uts *= expf(-alpha * alpha / (th * th));
+    const float w = (float)(p.n_cycles * p.lambda);
+    const float ul = expf(-zf * zf * 1.38629436111989061883f / (w * w));   // ln 4
+    return (float)(p.amp * sh.R0 / R) * carrier * ul * uts;
+}
+
+__device__ __forceinline__ void pol_vectors_f(float X, float Y, float Z, float d0, float d1, float d2, float s0[3],
+                                              float s1[3]) {
+    const float a0 = d1 * Z - d2 * Y, a1 = d2 * X - d0 * Z, a2 = d0 * Y - d1 * X;   // d x R
+    const float b0 = Y * a2 - Z * a1, b1 = Z * a0 - X * a2, b2 = X * a1 - Y * a0;   // R x (d x R)
+    const float n1 = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+    const float n0 = sqrtf(b0 * b0 + b1 * b1 + b2 * b2);
+    const float i1 = n1 > 0.f ? 1.f / n1 : 0.f, i0 = n0 > 0.f ? 1.f / n0 : 0.f;
+    s0[0] = b0 * i0; s0[1] = b1 * i0; s0[2] = b2 * i0;
+    s1[0] = a0 * i1; s1[1] = a1 * i1; s1[2] = a2 * i1;
+}
+
 template <typename T>
 __global__ void init_pulse_kernel(cplx<T>* __restrict__ data, GridGeom g, ShellGeom sh, PulseParams p,
                                   int m_lo, int m_hi) {
@@ -75,6 +130,32 @@ __global__ void init_pulse_kernel(cplx<T>* __restrict__ data, GridGeom g, ShellG
         const double xt = g.x_min + i * g.dx;
         const double y = g.y_min + j * g.dy;
         const double z = g.z_min + l * g.dz;
+        if constexpr (sizeof(T) == 4) {
+            const float cf = (float)cps, sf = (float)sps;
+            float E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+            for (int m = m_lo; m <= m_hi; ++m) {
+                const double x = xt + m * D;
+                const float u1 = pulse_u_f(x, y, z, p, sh, p.cep);
+                if (u1 != 0.f) {
+                    float s0[3], s1[3];
+                    pol_vectors_f((float)x, (float)y, (float)z, 0.f, cf, sf, s0, s1);
+                    for (int a = 0; a < 3; ++a) { E[a] += u1 * s0[a]; B[a] += u1 * s1[a]; }
+                }
+                if (p.ellipticity != 0.0) {
+                    const float u2 = (float)p.ellipticity * pulse_u_f(x, y, z, p, sh, p.cep + 0.5 * kPi);
+                    if (u2 != 0.f) {
+                        float s0[3], s1[3];
+                        pol_vectors_f((float)x, (float)y, (float)z, 0.f, -sf, cf, s0, s1);
+                        for (int a = 0; a < 3; ++a) { E[a] += u2 * s0[a]; B[a] += u2 * s1[a]; }
+                    }
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                data[a * n_cells + idx] = mk<T>((T)E[a], (T)0);
+                data[(3 + a) * n_cells + idx] = mk<T>((T)B[a], (T)0);
+            }
+            continue;
+        }
         double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
         for (int m = m_lo; m <= m_hi; ++m) {
             const double x = xt + m * D;
