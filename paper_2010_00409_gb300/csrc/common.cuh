@@ -50,6 +50,13 @@ __device__ __forceinline__ double cell_energy3(cplx<T> a, cplx<T> b, cplx<T> c) 
     return (double)s;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel's last blocks still run;
+// it must call pdl_wait() before touching that kernel's output.  Both are no-ops
+// for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // 1D plan of one axis: N = prod(radix[0..npass)), radices in {2,3,4,5,8}
 // ---------------------------------------------------------------------------

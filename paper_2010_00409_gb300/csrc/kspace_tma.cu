@@ -64,21 +64,19 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     const int xt = blockIdx.x % ntile;
     const int y = blockIdx.x / ntile;
     const int ix = xt * W + c;
+    pdl_launch_dependents();
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, kBytes);
-        constexpr int xw = (int)(sizeof(cplx<T>) / 8);        // 8-byte elements per complex
-        for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
-    }
 
-    // while the copies fly: outer twiddles W_N^{j k1} (the inverse uses their
-    // conjugates with k1 = j) and the per-mode coefficients of this thread's
-    // modes (registers r = h NM .. h NM + NM - 1 of position (c, j))
+    // before the field is read (this part may overlap the previous kernel):
+    // outer twiddles W_N^{j k1} (the inverse uses their conjugates with k1 = j)
+    // and the per-mode coefficients of this thread's modes (registers
+    // r = h NM .. h NM + NM - 1 of position (c, j)); their loads complete while
+    // the tile copies fly
     cplx<T> twr[N1];
     static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
     const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
@@ -94,6 +92,13 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         mc[m] = coef[((size_t)az * Nyh + ay) * Nxh + ax];
         kzr[m] = kzs[iz];
     });
+
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, kBytes);
+        constexpr int xw = (int)(sizeof(cplx<T>) / 8);        // 8-byte elements per complex
+        for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
+    }
 
     if (threadIdx.x == 0) {
         bool ok = mbar_wait_bounded(&bar, 0);
@@ -256,10 +261,19 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     if (e != cudaSuccess) return e;
     const int nx = half ? g.Nx / 2 : g.Nx;             // complex elements per stored row
     const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W));
-    k<<<blocks, W * N2 * G, smem, s>>>(map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
-                                       half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
-                                       half ? half->side : nullptr);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(W * N2 * G, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // real-field step: overlap the tail
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = half ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
+                              half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
+                              half ? half->side : (cplx<T>*)nullptr);
 }
 
 // Self-test of the bounded-wait path: waits on an mbarrier whose 16 expected

@@ -86,11 +86,13 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);
 
+    pdl_launch_dependents();
     cg::cluster_group cluster = cg::this_cluster();
     cluster.barrier_arrive();                          // wait for all blocks before the first remote store
     const int r = (int)cluster.block_rank();
     float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
     const int tid = threadIdx.x;
+    pdl_wait();
 
     // ---------------- phase 1: stage A of rows 32 r .. 32 r + 31, scatter by k1
     {
@@ -170,10 +172,12 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);   // [256][16] this block's columns, then [16][8][32] rows
 
+    pdl_launch_dependents();
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
     float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
     const int tid = threadIdx.x;
+    pdl_wait();
 
     // ---------------- phase 1: inverse y on slots 16 r .. 16 r + 15
     {
@@ -273,13 +277,15 @@ cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tab
     cfg.blockDim = dim3(kRcThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kRcC;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;     // may overlap the previous kernel's tail
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     float2* d = reinterpret_cast<float2*>(data);
     if (dir < 0) return cudaLaunchKernelEx(&cfg, plane_r2c_kernel, d, tb.tw[0], tb.tw[1]);
     return cudaLaunchKernelEx(&cfg, plane_c2r_kernel, d, tb.tw[0], tb.tw[1]);

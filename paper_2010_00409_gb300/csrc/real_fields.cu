@@ -31,6 +31,8 @@ kspace_x0_kernel(float2* __restrict__ data, const float2* __restrict__ side, int
     float2* b = a + 6 * Nz;
     const int y = blockIdx.x, ym = (Ny - y) % Ny;          // this pencil and its mirror
     const size_t plane = (size_t)Nh * Ny, cstride = plane * Nz;
+    pdl_launch_dependents();
+    pdl_wait();
 
     const int Nyh = Ny / 2 + 1, ax_nyq = Nxh - 1;
     for (int kz = threadIdx.x; kz < Nz; kz += blockDim.x) {
@@ -84,10 +86,19 @@ cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float
     const size_t smem = (size_t)2 * 6 * g.Nz * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(kspace_x0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kspace_x0_kernel<<<g.Ny, kX0Threads, smem, s>>>(data, hs.side, g.Nx / 2, g.Ny, g.Nz, tb.plan[2], tb.tw[2],
-                                                            (float)(-3.14159265358979323846 / g.dx), tb.k[1], tb.k[2],
-                                                            hs.coef, g.Nx / 2 + 1);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.Ny, 1, 1);
+    cfg.blockDim = dim3(kX0Threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;     // may overlap the previous kernel's tail
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kspace_x0_kernel, data, (const float2*)hs.side, g.Nx / 2, g.Ny, g.Nz, tb.plan[2],
+                              tb.tw[2], (float)(-3.14159265358979323846 / g.dx), tb.k[1], tb.k[2], hs.coef,
+                              g.Nx / 2 + 1);
 }
 
 cudaError_t launch_widen(const float* in, float2* out, size_t n, cudaStream_t s) {
