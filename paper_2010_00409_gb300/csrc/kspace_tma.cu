@@ -267,10 +267,10 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // real-field step: overlap the tail
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // may overlap the previous kernel's tail
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = half ? 1 : 0;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
                               half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
                               half ? half->side : (cplx<T>*)nullptr);

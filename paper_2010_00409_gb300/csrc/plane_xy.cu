@@ -42,6 +42,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* slab = reinterpret_cast<cplx<T>*>(smem_raw);       // [NY][COLS]
 
+    pdl_launch_dependents();
     cg::cluster_group cluster = cg::this_cluster();
     // every block of the cluster must have started before its shared memory is
     // written remotely: arrive now, wait just before the first remote store
@@ -49,6 +50,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
     const int r = (int)cluster.block_rank();
     const long long plane_id = blockIdx.x / C;
     cplx<T>* plane = data + plane_id * (long long)(NX * NY);
+    pdl_wait();                                        // the previous kernel's output is read below
 
     // ---------------- phase 1: rows along x, exchange by lane transpose
     {
@@ -151,13 +153,15 @@ cudaError_t plane_launch(cplx<T>* data, int ncomp, int Nz, const cplx<T>* twx, c
     cfg.blockDim = dim3(kPlaneThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;     // may overlap the previous kernel's tail
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, data, twx, twy);
 }
 
