@@ -39,7 +39,7 @@ from paper_2010_00409_gb300 import workloads as W  # noqa: E402
 
 METRIC = "PSATD cell-steps/s"
 UNIT = "cell-steps/s"
-STEP_KERNELS = ("fft_x", "fft_y", "fft_z", "kspace_z", "plane_xy", "kspace_x0")
+STEP_KERNELS = ("fft_x", "fft_y", "fft_z", "kspace_z", "plane_xy")
 # algorithmic bytes per cell of one full-field sweep (six components read and written)
 SWEEP_BYTES = {"real": 48, "complex": 96}
 FALLBACK_HBM_GBS = 6800.0
@@ -313,11 +313,9 @@ def step_roofline(prof, g, storage, size, peak, peak_src):
     dom_ms, dom_n = step_k[dom]
     bytes_per_launch = B * g.cells
     achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
-    # the packed-slot kernel touches the k_x = 0 pencils only: 6 x Ny x Nz complex64 read + write
-    per_launch = {k: (96 * g.Ny * g.Nz if k == "kspace_x0" else B * g.cells) for k in step_k}
-    sweep_bytes = sum(per_launch[k] * v[1] for k, v in step_k.items())
+    sweep_bytes = sum(B * g.cells * v[1] for v in step_k.values())
     step_total = sum(v[0] for v in step_k.values())
-    n_full = sum(v[1] for k, v in step_k.items() if k != "kspace_x0")
+    n_full = sum(v[1] for v in step_k.values())
     n_st = step_k.get("kspace_z", (0.0, 0))[1] or max(n_full // 3, 1)     # one k-space launch per step
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"

@@ -337,8 +337,7 @@ enum {
     PSATD_KERNEL_SAMPLE = 5,     /* focal-plane sampling (all of its launches) */
     PSATD_KERNEL_DIAG = 6,       /* energy / divergence reductions */
     PSATD_KERNEL_PLANE_XY = 7,   /* fused x+y plane FFT (real fields: r2c / c2r plane kernels) */
-    PSATD_KERNEL_KSPACE_X0 = 8,  /* real fields: the packed k_x = 0 / Nyquist slot */
-    PSATD_KERNEL_KINDS = 9
+    PSATD_KERNEL_KINDS = 8
 };
 
 /* Start (enable != 0) or stop per-kernel timing: while enabled every launch of

@@ -131,12 +131,13 @@ cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>
 // kernels: per slot p < Nx/2 the wave number k_x, and the coefficient table
 // with its x index in slot order (column p = slot p, column Nx/2 = the x
 // Nyquist mode), (Nz/2+1) x (Ny/2+1) x (Nx/2+1) entries.
-// side: [6][Ny][Nz] complex, the z spectra of slot 0 handed from the k-space
-// pass to the slot-0 pass.
+// nyq: [6][Nz][Ny] complex, the x Nyquist spectrum of the real fields, and
+// map_nyq its 3D tensor map {Ny * sizeof(complex)/8, Nz, 6} (box {W, Nz, 1}).
 template <typename T> struct HalfSlots {
     const T* k;
     const ModeCoef<T>* coef;
-    cplx<T>* side;
+    cplx<T>* nyq;
+    const CUtensorMap* map_nyq;
 };
 
 // Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
@@ -149,17 +150,12 @@ cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridG
                               int* err, cudaStream_t s, bool spectral_out = false, bool project_b = false,
                               const HalfSlots<T>* half = nullptr);
 
-// Slot 0 of a real-field half spectrum (k_x = 0 packed with the x Nyquist
-// mode): unpack the two Hermitian spectra, apply the update, repack; all six
-// components, z transforms included.
-cudaError_t launch_kspace_x0(float2* data, const GridGeom& g, const Tables<float>& tb, const HalfSlots<float>& hs,
-                             cudaStream_t s);
-
 // Real-field plane transforms (FP32, 256 x 256 planes, in place): dir < 0 =
 // r2c along x + y, dir > 0 = inverse y + c2r.  Spectra are in slot order
-// (plane_rc_slot_mode(p) = x mode index of slot p).
-cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
-                            cudaStream_t s);
+// (plane_rc_slot_mode(p) = x mode index of slot p); the x Nyquist spectrum goes
+// to / comes from nyq [ncomp * Nz][Ny].
+cudaError_t launch_plane_rc(float* data, float2* nyq, int ncomp, const GridGeom& g, const Tables<float>& tb,
+                            int dir, cudaStream_t s);
 bool plane_rc_supported(int prec, const GridGeom& g);
 int plane_rc_slot_mode(int p);
 

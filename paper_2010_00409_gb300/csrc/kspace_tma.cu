@@ -31,16 +31,18 @@ namespace {
 // HALF: the storage holds the half spectrum of real fields in the slot order of
 // the real-field plane kernels (x extent = Nx/2 slots): the slot's wave number
 // comes from kxs and the coefficient table is in slot order along x (column =
-// slot, so neighbouring threads read neighbouring entries), modes on the y or z
-// Nyquist planes take the mean update that keeps the field real, and slot 0
-// (k_x = 0 packed with the x Nyquist mode) is left to kspace_x0_kernel: its
-// z spectra go to side[component][y][k_z] and the field keeps slot 0 unchanged.
+// slot, so neighbouring threads read neighbouring entries; column Nx/2 = the x
+// Nyquist mode), and modes on Nyquist planes take the mean update that keeps the
+// field real.  The x Nyquist spectrum lives in its own array nyq[q][z][k_y]; the
+// blocks after the Ny * Nx/(2W) field tiles take its tiles of W k_y values
+// (copied through map_nyq, a 3D map {Ny, Nz, 6}).
 template <typename T, int N1, int N2, int W, int G, bool SPECTRAL_OUT, bool HALF>
 __global__ void __launch_bounds__(W * N2 * G)
-kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__ data, int Nx, int Ny,
-                  const cplx<T>* __restrict__ tw, const T* __restrict__ kxs, const T* __restrict__ kys,
-                  const T* __restrict__ kzs, const ModeCoef<T>* __restrict__ coef, int* __restrict__ err,
-                  bool project_b, int coef_nx, cplx<T>* __restrict__ side) {
+kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_nyq,
+                  cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __restrict__ tw,
+                  const T* __restrict__ kxs, const T* __restrict__ kys, const T* __restrict__ kzs,
+                  const ModeCoef<T>* __restrict__ coef, int* __restrict__ err, bool project_b, int coef_nx,
+                  cplx<T>* __restrict__ nyq, T kx_nyq) {
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
@@ -58,12 +60,14 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
 
     const int t = threadIdx.x % NT, h = threadIdx.x / NT;       // group h: components NC h .. NC h + NC - 1
     const int c = t % W, j = t / W;
-    const size_t plane = (size_t)Nx * Ny;
-    const size_t cstride = plane * Nz;
     const int ntile = Nx / W;
-    const int xt = blockIdx.x % ntile;
-    const int y = blockIdx.x / ntile;
-    const int ix = xt * W + c;
+    const bool nq = HALF && (int)blockIdx.x >= ntile * Ny;      // a tile of the x Nyquist array
+    const int bt = nq ? (int)blockIdx.x - ntile * Ny : (int)blockIdx.x;
+    const int xt = nq ? 0 : bt % ntile;
+    const int y = nq ? bt * W + c : bt / ntile;                 // this thread's k_y index
+    const int ix = nq ? 0 : xt * W + c;
+    const size_t plane = nq ? (size_t)Ny : (size_t)Nx * Ny;
+    const size_t cstride = plane * Nz;
     pdl_launch_dependents();
 
     if (threadIdx.x == 0) {
@@ -80,8 +84,8 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     cplx<T> twr[N1];
     static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
     const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
-    const int ax = HALF ? ix : min(ix, Nx - ix), ay = min(y, Ny - y);
-    const T kx = kxs[ix], ky = kys[y];
+    const int ax = HALF ? (nq ? coef_nx - 1 : ix) : min(ix, Nx - ix), ay = min(y, Ny - y);
+    const T kx = nq ? kx_nyq : kxs[ix], ky = kys[y];
     ModeCoef<T> mc[NM];
     T kzr[NM];
     static_for<0, NM>([&](auto mcix) {
@@ -97,7 +101,10 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&bar, kBytes);
         constexpr int xw = (int)(sizeof(cplx<T>) / 8);        // 8-byte elements per complex
-        for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
+        if (nq)
+            for (int q = 0; q < 6; ++q) tma_load_3d(spec + q * SLOT, &map_nyq, &bar, bt * W * xw, 0, q);
+        else
+            for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
     }
 
     if (threadIdx.x == 0) {
@@ -150,17 +157,6 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     }
     if constexpr (G > 1) __syncthreads();                      // the update reads the other group's components
 
-    if constexpr (HALF) {
-        if (ix == 0) {
-            static_for<0, NM>([&](auto mcix) {
-                const int r = h * NM + decltype(mcix)::value;
-                const int iz = (j + N2 * (r / N2)) + N1 * (r % N2);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) side[((size_t)q * Ny + y) * Nz + iz] = own[q * SLOT + r * RP];
-            });
-        }
-    }
-
     // per-mode update on this thread's modes of position (c, j)
     static_for<0, NM>([&](auto mcix) {
         constexpr int m = decltype(mcix)::value;
@@ -171,8 +167,8 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
         const ModeCoef<T> mm = mc[m];
         if constexpr (HALF) {
             const bool fz = ((j + N2 * (r / N2)) + N1 * (r % N2)) == Nz / 2;
-            rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, false,
-                                y == Ny / 2, fz, mm.C, mm.S);
+            rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq,
+                                2 * y == Ny, fz, mm.C, mm.S);
         } else {
             rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, mm.C, mm.S,
                            project_b);
@@ -182,7 +178,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
     });
     if constexpr (G > 1) __syncthreads();                      // the inverse reads the other group's modes
 
-    cplx<T>* base = data + (size_t)y * Nx + ix;
+    cplx<T>* base = nq ? nyq + y : data + (size_t)y * Nx + ix;
     if constexpr (SPECTRAL_OUT) {
         // store the updated spectrum in natural kz order (one-shot focal path)
         for (int q = NC * h; q < NC * h + NC; ++q) {
@@ -240,8 +236,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, cplx<T>* __restrict__
             constexpr int b = decltype(bc)::value;
             reg_dft<T, +1, N1>(v[b]);
             cplx<T>* p = base + (q0 + b) * cstride;
-            if (!HALF || ix != 0)
-                static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
+            static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
         });
     }
 }
@@ -260,7 +255,7 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nx = half ? g.Nx / 2 : g.Nx;             // complex elements per stored row
-    const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W));
+    const unsigned blocks = (unsigned)((long long)g.Ny * (nx / W) + (half ? g.Ny / W : 0));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks, 1, 1);
     cfg.blockDim = dim3(W * N2 * G, 1, 1);
@@ -271,9 +266,10 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, map, data, nx, g.Ny, tb.tw[2], half ? half->k : tb.k[0], tb.k[1], tb.k[2],
-                              half ? half->coef : tb.coef, err, project_b, g.Nx / 2 + 1,
-                              half ? half->side : (cplx<T>*)nullptr);
+    return cudaLaunchKernelEx(&cfg, k, map, half ? *half->map_nyq : map, data, nx, g.Ny, tb.tw[2],
+                              half ? half->k : tb.k[0], tb.k[1], tb.k[2], half ? half->coef : tb.coef, err, project_b,
+                              g.Nx / 2 + 1, half ? half->nyq : (cplx<T>*)nullptr,
+                              (T)(-3.14159265358979323846 / g.dx));
 }
 
 // Self-test of the bounded-wait path: waits on an mbarrier whose 16 expected
@@ -305,7 +301,8 @@ template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
                               int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     constexpr int W = kspace_tma_width<T>();
-    if ((half ? g.Nx / 2 : g.Nx) % W != 0 || (half && (spectral_out || project_b))) return cudaErrorNotSupported;
+    if ((half ? g.Nx / 2 : g.Nx) % W != 0 || (half && (spectral_out || project_b || g.Ny % W != 0)))
+        return cudaErrorNotSupported;
     switch (g.Nz) {
         case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);
         case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);

@@ -7,7 +7,11 @@
 // (in the registers of lane j), stage B = 8-point DFT over j.  The real-to-
 // complex step pairs Z[k] with Z[128-k]:
 //   X[k] = (Z[k] + conj Z[128-k])/2 + W_256^k (Z[k] - conj Z[128-k])/(2i),
-// and X[0], X[128] (both real) share slot 0 as X[0] + i X[128].
+// and X[0], X[128] (both real) share slot 0 as X[0] + i X[128] through the y
+// transform; block 0 then unpacks the column with its mirror k_y
+//   S0 = (P(k_y) + conj P(-k_y)) / 2,   SN = (P(k_y) - conj P(-k_y)) / (2i)
+// and stores S0 (the k_x = 0 spectrum) in slot 0 and SN (the x Nyquist spectrum)
+// in a separate array nyq[plane][k_y]; the inverse repacks S0 + i SN pointwise.
 //
 // A cluster of 8 blocks owns one plane.  Block r owns the stage-A outputs with
 // k1 in {r, 16-r} (block 0: {0, 8}); those are exactly the k that pair with each
@@ -82,9 +86,11 @@ __device__ __forceinline__ void c2r_pair(float2 X, float2 P, float2 w, float2* a
 }
 
 __global__ void __launch_bounds__(kRcThreads)
-plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy) {
+plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
+                 float2* __restrict__ nyq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);
+    __shared__ float2 col0[kNy];                       // block 0: the packed column after the y transform
 
     pdl_launch_dependents();
     cg::cluster_group cluster = cg::this_cluster();
@@ -159,6 +165,20 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
         __syncthreads();
         static_for<0, 16>([&](auto jc) { v[decltype(jc)::value] = tile[sw16(16 * jy + decltype(jc)::value, c)]; });
         reg_dft<float, -1, 16>(v);                     // v[k2] = Y[jy + 16 k2]
+        if (r == 0) {                                  // unpack slot 0 (block-uniform branch)
+            if (c == 0) static_for<0, 16>([&](auto kc) { col0[jy + 16 * decltype(kc)::value] = v[decltype(kc)::value]; });
+            __syncthreads();
+            if (c == 0) {
+                float2* nq = nyq + (size_t)(blockIdx.x / kRcC) * kNy;
+                static_for<0, 16>([&](auto kc) {
+                    constexpr int k2 = decltype(kc)::value;
+                    const int ky = jy + 16 * k2;
+                    const float2 P = v[k2], Pm = col0[(kNy - ky) & (kNy - 1)];
+                    v[k2] = make_float2(0.5f * (P.x + Pm.x), 0.5f * (P.y - Pm.y));
+                    nq[ky] = make_float2(0.5f * (P.y + Pm.y), -0.5f * (P.x - Pm.x));
+                });
+            }
+        }
         float2* out = plane + 16 * r + c;
         static_for<0, 16>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
@@ -168,7 +188,8 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
 }
 
 __global__ void __launch_bounds__(kRcThreads)
-plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy) {
+plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
+                 const float2* __restrict__ nyq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);   // [256][16] this block's columns, then [16][8][32] rows
 
@@ -185,6 +206,14 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
         const float2* in = plane + 16 * r + c;
         float2 v[16];
         static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = in[(size_t)(jy + 16 * decltype(kc)::value) * kM]; });
+        if (r == 0 && c == 0) {                        // repack slot 0: S0 + i SN
+            const float2* nq = nyq + (size_t)(blockIdx.x / kRcC) * kNy;
+            static_for<0, 16>([&](auto kc) {
+                constexpr int k2 = decltype(kc)::value;
+                const float2 sn = nq[jy + 16 * k2];
+                v[k2] = make_float2(v[k2].x - sn.y, v[k2].y + sn.x);
+            });
+        }
         reg_dft<float, +1, 16>(v);                     // over k2, k1 = jy
         static_for<0, 16>([&](auto nc) {
             constexpr int n2 = decltype(nc)::value;
@@ -268,7 +297,7 @@ bool plane_rc_supported(int prec, const GridGeom& g) { return prec == 32 && g.Nx
 
 // Real-field plane transform of ncomp components (dir < 0: r2c + y, dir > 0:
 // inverse y + c2r) of real FP32 fields [ncomp][Nz][256][256], in place.
-cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
+cudaError_t launch_plane_rc(float* data, float2* nyq, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
                             cudaStream_t s) {
     if (!plane_rc_supported(32, g)) return cudaErrorNotSupported;
     const size_t smem = (size_t)kM * kNy / kRcC * sizeof(float2);    // 32 KB
@@ -287,12 +316,12 @@ cudaError_t launch_plane_rc(float* data, int ncomp, const GridGeom& g, const Tab
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     float2* d = reinterpret_cast<float2*>(data);
-    if (dir < 0) return cudaLaunchKernelEx(&cfg, plane_r2c_kernel, d, tb.tw[0], tb.tw[1]);
-    return cudaLaunchKernelEx(&cfg, plane_c2r_kernel, d, tb.tw[0], tb.tw[1]);
+    if (dir < 0) return cudaLaunchKernelEx(&cfg, plane_r2c_kernel, d, tb.tw[0], tb.tw[1], nyq);
+    return cudaLaunchKernelEx(&cfg, plane_c2r_kernel, d, tb.tw[0], tb.tw[1], (const float2*)nyq);
 }
 
 // Slot order of the spectra the plane kernels leave in storage: the x mode
-// index 0..127 held by slot p (slot 0 also holds the Nyquist mode 128).
+// index 0..127 held by slot p (the x Nyquist mode is kept apart, see above).
 int plane_rc_slot_mode(int p) {
     const int r = p / 16, s = (p / 8) & 1, k2 = p & 7;
     const int k1 = r == 0 ? (s ? 8 : 0) : (s ? 16 - r : r);

@@ -86,7 +86,9 @@ struct psatd_ctx {
     bool real_fields = false;           // real float32 storage (PSATD_FLAG_REAL_FIELDS)
     DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
     DevBuf slot_k, slot_coef;           // real fields: k_x per slot, coefficient table in slot order
-    DevBuf slot0_side;                  // real fields: z spectra of slot 0 between the k-space passes
+    DevBuf nyq;                         // real fields: x Nyquist spectrum [6][Nz][Ny] between the plane kernels
+    alignas(64) CUtensorMap nyq_map;    // ... and its tensor map for the k-space kernel
+    bool nyq_map_ok = false;
 
     // tables (device)
     DevBuf tw[3], k[3], coef;
@@ -487,35 +489,30 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     return cudaSuccess;
 }
 
-// One real-field step: r2c plane transforms, the half-spectrum k-space pass,
-// the packed slot-0 pass, c2r plane transforms.
+// One real-field step: r2c plane transforms, the half-spectrum k-space pass
+// (field slots and the x Nyquist array in one launch), c2r plane transforms.
 cudaError_t spectral_pass_real(psatd_ctx* c) {
     const GridGeom g = geom(c);
     const Tables<float> tb = tables<float>(c);
     float* f = static_cast<float*>(c->fields);
+    float2* nyq = static_cast<float2*>(c->nyq.p);
     cudaError_t e = timed(c, PSATD_KERNEL_PLANE_XY, [&] {
         ++c->launches;
-        return launch_plane_rc(f, 6, g, tb, -1, c->stream);
+        return launch_plane_rc(f, nyq, 6, g, tb, -1, c->stream);
     });
     if (e != cudaSuccess) return e;
-    if (!ensure_field_map(c)) return cudaErrorNotSupported;
+    if (!ensure_field_map(c) || !c->nyq_map_ok) return cudaErrorNotSupported;
     const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p),
-                              static_cast<const ModeCoef<float>*>(c->slot_coef.p),
-                              static_cast<float2*>(c->slot0_side.p)};
+                              static_cast<const ModeCoef<float>*>(c->slot_coef.p), nyq, &c->nyq_map};
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
         ++c->launches;
         return launch_kspace_tma<float>(c->field_map, reinterpret_cast<cplx<float>*>(f), g, tb, c->dev_err, c->stream,
                                         false, false, &hs);
     });
     if (e != cudaSuccess) return e;
-    e = timed(c, PSATD_KERNEL_KSPACE_X0, [&] {
-        ++c->launches;
-        return launch_kspace_x0(reinterpret_cast<float2*>(f), g, tb, hs, c->stream);
-    });
-    if (e != cudaSuccess) return e;
     return timed(c, PSATD_KERNEL_PLANE_XY, [&] {
         ++c->launches;
-        return launch_plane_rc(f, 6, g, tb, +1, c->stream);
+        return launch_plane_rc(f, nyq, 6, g, tb, +1, c->stream);
     });
 }
 
@@ -555,7 +552,20 @@ psatd_status upload_slot_tables(psatd_ctx* c) {
         k[p] = (float)(kTwoPi * (double)plane_rc_slot_mode(p) / (c->grid.Nx * c->grid.dx));
     CK(c, ensure_buf(c->slot_k, nh * sizeof(float)));
     CK(c, cudaMemcpy(c->slot_k.p, k.data(), nh * sizeof(float), cudaMemcpyHostToDevice));
-    CK(c, ensure_buf(c->slot0_side, (size_t)6 * c->grid.Ny * c->grid.Nz * sizeof(float2)));
+    const size_t nn = (size_t)6 * c->grid.Ny * c->grid.Nz;
+    CK(c, ensure_buf(c->nyq, nn * sizeof(float2)));
+    CK(c, cudaMemset(c->nyq.p, 0, nn * sizeof(float2)));
+    // 3D map {Ny, Nz, 6} of 8-byte elements, box {kspace_tma_box_x, Nz, 1}
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc && kspace_tma_box_z(c->grid.Nz)) {
+        const cuuint64_t dims[3] = {(cuuint64_t)c->grid.Ny, (cuuint64_t)c->grid.Nz, 6};
+        const cuuint64_t strides[2] = {(cuuint64_t)c->grid.Ny * 8, (cuuint64_t)c->grid.Ny * c->grid.Nz * 8};
+        const cuuint32_t box[3] = {(cuuint32_t)kspace_tma_box_x(32), (cuuint32_t)kspace_tma_box_z(c->grid.Nz), 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        c->nyq_map_ok = enc(&c->nyq_map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, c->nyq.p, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     return PSATD_OK;
 }
 
@@ -704,7 +714,7 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef);
     free_buf(c->coef_T);
     free_buf(c->coef_proj);
-    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->slot0_side);
+    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
@@ -1267,7 +1277,7 @@ psatd_status psatd_profile_read(psatd_ctx* c, int kind, double* total_ms, long l
 const char* psatd_kernel_name(int kind) {
     static const char* names[PSATD_KERNEL_KINDS] = {"fft_x", "fft_y", "fft_z", "kspace_z",
                                                     "init_pulse", "sample_plane", "diagnostics",
-                                                    "plane_xy", "kspace_x0"};
+                                                    "plane_xy"};
     return (kind >= 0 && kind < PSATD_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 

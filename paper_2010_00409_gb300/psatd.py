@@ -38,7 +38,7 @@ EXPORTS = (
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
 KERNEL_KINDS = ("fft_x", "fft_y", "fft_z", "kspace_z", "init_pulse", "sample_plane", "diagnostics",
-                "plane_xy", "kspace_x0")
+                "plane_xy")
 
 
 class PsatdGrid(C.Structure):
