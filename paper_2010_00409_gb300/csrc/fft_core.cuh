@@ -16,17 +16,63 @@
 
 namespace psatd {
 
+// Complex sum and difference of butterfly operands.  float32 pairs on the GPU
+// use the packed two-lane adds of sm_100-class SMs (add/sub.rn.f32x2: one
+// instruction per complex add, the same round-to-nearest result as two scalar
+// adds); double pairs and host code use cadd / csub.
+template <typename V> __host__ __device__ __forceinline__ V badd(V a, V b) { return cadd(a, b); }
+template <typename V> __host__ __device__ __forceinline__ V bsub(V a, V b) { return csub(a, b); }
+__host__ __device__ __forceinline__ float2 badd(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    float2 r;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+#else
+    return cadd(a, b);
+#endif
+}
+__host__ __device__ __forceinline__ float2 bsub(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    float2 r;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+#else
+    return csub(a, b);
+#endif
+}
+
+// t + S i u and t - S i u in scalar form: the lane swap of i u does not pack.
+template <typename V, int S>
+__host__ __device__ __forceinline__ void add_sub_si(const V& t, const V& u, V& plus, V& minus) {
+    if constexpr (S > 0) {
+        plus.x = t.x - u.y; plus.y = t.y + u.x;
+        minus.x = t.x + u.y; minus.y = t.y - u.x;
+    } else {
+        plus.x = t.x + u.y; plus.y = t.y - u.x;
+        minus.x = t.x - u.y; minus.y = t.y + u.x;
+    }
+}
+
 template <typename V, int S>
 __host__ __device__ __forceinline__ void bfly2(V& a0, V& a1) {
-    V t = a0; a0 = cadd(t, a1); a1 = csub(t, a1);
+    V t = a0; a0 = badd(t, a1); a1 = bsub(t, a1);
 }
 
 template <typename V, int S>
 __host__ __device__ __forceinline__ void bfly4(V& a0, V& a1, V& a2, V& a3) {
-    V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
-    V t3 = cmul_si(csub(a1, a3), S);
-    a0 = cadd(t0, t2); a2 = csub(t0, t2);
-    a1 = cadd(t1, t3); a3 = csub(t1, t3);
+    V t0 = badd(a0, a2), t1 = bsub(a0, a2), t2 = badd(a1, a3), u = bsub(a1, a3);
+    a0 = badd(t0, t2); a2 = bsub(t0, t2);
+    add_sub_si<V, S>(t1, u, a1, a3);                 // t1 +- S i (a1 - a3)
 }
 
 template <typename T, int S>
@@ -38,15 +84,13 @@ __host__ __device__ __forceinline__ void bfly8(cplx<T>* v) {
     cplx<T> o1 = v[3], o2 = v[5], o3 = v[7];
     // W^1 = (1 + S i)/sqrt2
     cplx<T> w1 = mk<T>(r * (o1.x - S * o1.y), r * (o1.y + S * o1.x));
-    // W^2 = S i
-    cplx<T> w2 = cmul_si(o2, S);
     // W^3 = (-1 + S i)/sqrt2
     cplx<T> w3 = mk<T>(-r * (o3.x + S * o3.y), r * (S * o3.x - o3.y));
     cplx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
-    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-    v[1] = cadd(e1, w1); v[5] = csub(e1, w1);
-    v[2] = cadd(e2, w2); v[6] = csub(e2, w2);
-    v[3] = cadd(e3, w3); v[7] = csub(e3, w3);
+    v[0] = badd(e0, o0); v[4] = bsub(e0, o0);
+    v[1] = badd(e1, w1); v[5] = bsub(e1, w1);
+    add_sub_si<cplx<T>, S>(e2, o2, v[2], v[6]);     // W^2 = S i
+    v[3] = badd(e3, w3); v[7] = bsub(e3, w3);
 }
 
 template <typename T, int S>

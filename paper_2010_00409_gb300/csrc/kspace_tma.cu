@@ -1,22 +1,38 @@
 // Fused k-space pass of one PSATD step (Sec. 2.1, Eq. 3-4), fed by the tensor
 // copy engine: at block start one thread issues six tiled bulk-tensor loads
 // (one per field component, box = W x-columns x 1 y x Nz z, 64 contiguous bytes
-// per row) into the six shared-memory slots, all completing on one mbarrier.
-// The whole tile (6 * Nz * W complex values) is then in flight at once, while
-// the other resident block computes.  The block's threads form two groups; each
-// group transforms three components.  Per component: forward z transform in
-// registers (the slot doubles as the exchange buffer), spectrum back to the
-// slot; the per-mode update over all six slots (modes split between the
-// groups); inverse z transforms stored straight from registers to the field.
+// per row) into the six shared-memory slots, each completing on its own
+// mbarrier.  The whole tile (6 * Nz * W complex values) is then in flight at
+// once; each thread group starts on its first component as soon as that slot
+// has landed.  The block's threads form two groups; each group transforms
+// three components.  Per component: forward z transform in registers (the slot
+// doubles as the exchange buffer; the exchanges synchronise only the group, on
+// a named barrier), spectrum back to the slot; the per-mode update over all six
+// slots (modes split between the groups, block-wide barriers around it);
+// inverse z transforms stored straight from registers to the field.
 //
-// The wait on the copies is bounded: past the limit the block sets an error bit
-// in the context's device error word and returns without touching the field.
+// The waits on the copies are bounded: past the limit the block sets an error
+// bit in the context's device error word and runs on with invalid data.
 #include "fft_reg.cuh"
 #include "tma.cuh"
 
 namespace psatd {
 
 namespace {
+
+// Barrier over the NT threads of group h only (named barrier 1 + h; barrier 0
+// is __syncthreads): the exchange rounds of a group touch only its own
+// components' slots, so the other group need not wait.
+template <int NT, int G>
+__device__ __forceinline__ void group_sync(int h) {
+    if constexpr (G > 1) {
+        // immediate barrier ids, so that the block claims three barriers, not all sixteen
+        if (h == 0) asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+        else asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+    } else {
+        __syncthreads();
+    }
+}
 
 // Shared-memory layout of one component slot: element (row k1, lane j, column c)
 // at k1*RP + j*W + c with RP = N2*W, i.e. the dense [z][c] tile the copy engine
@@ -55,8 +71,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     static_assert(NC % NB == 0 && N1 % G == 0, "group split");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cplx<T>* spec = reinterpret_cast<cplx<T>*>(smem_raw);      // [6][N1][RP]
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int failed;
+    __shared__ __align__(8) uint64_t bar[6];                    // one mbarrier per component slot
 
     const int t = threadIdx.x % NT, h = threadIdx.x / NT;       // group h: components NC h .. NC h + NC - 1
     const int c = t % W, j = t / W;
@@ -71,7 +86,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     pdl_launch_dependents();
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+        for (int q = 0; q < 6; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -99,24 +114,28 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
 
     pdl_wait();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, kBytes);
         constexpr int xw = (int)(sizeof(cplx<T>) / 8);        // 8-byte elements per complex
-        if (nq)
-            for (int q = 0; q < 6; ++q) tma_load_3d(spec + q * SLOT, &map_nyq, &bar, bt * W * xw, 0, q);
-        else
-            for (int q = 0; q < 6; ++q) tma_load_4d(spec + q * SLOT, &map, &bar, xt * W * xw, y, 0, q);
+        for (int i = 0; i < 6; ++i) {
+            // each group's first component first (0, 3, 1, 4, 2, 5 for two groups)
+            const int q = (i % G) * NC + i / G;
+            mbar_arrive_expect_tx(&bar[q], kBytes / 6);
+            if (nq) tma_load_3d(spec + q * SLOT, &map_nyq, &bar[q], bt * W * xw, 0, q);
+            else tma_load_4d(spec + q * SLOT, &map, &bar[q], xt * W * xw, y, 0, q);
+        }
     }
 
-    if (threadIdx.x == 0) {
-        bool ok = mbar_wait_bounded(&bar, 0);
-        if (!ok) {
-            atomicOr(err, DEV_ERR_TMA_TIMEOUT);
-            mbar_wait_bounded(&bar, 0);                        // give copies in flight a second chance
-        }
-        failed = ok ? 0 : 1;
-    }
-    __syncthreads();
-    if (failed) return;
+    // every thread waits for a component just before its first read of it, so
+    // a group starts on its first component while the others are in flight; an
+    // expired wait records the error and the block runs on (its barriers stay
+    // matched), and the block's last act is a second bounded wait on every copy
+    // so that none is in flight when it exits
+    auto wait_slot = [&](int q) {
+        if (!mbar_wait_bounded(&bar[q], 0) && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_TMA_TIMEOUT);
+    };
+    auto drain = [&]() {
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 6; ++q) mbar_wait_bounded(&bar[q], 0);
+    };
 
     cplx<T>* own = spec + j * W + c;                           // (row r, position (c, j)) at own[r * RP]
     cplx<T> v[NB][N1];
@@ -126,6 +145,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     for (int q0 = NC * h; q0 < NC * h + NC; q0 += NB) {
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
+            wait_slot(q0 + b);
             cplx<T>* sl = own + (q0 + b) * SLOT;
             static_for<0, N1>([&](auto nc) { v[b][decltype(nc)::value] = sl[decltype(nc)::value * RP]; });
             reg_dft<T, -1, N1>(v[b]);
@@ -135,7 +155,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
             });
             static_for<0, N1>([&](auto kc) { sl[decltype(kc)::value * RP] = v[b][decltype(kc)::value]; });
         });
-        __syncthreads();
+        group_sync<NT, G>(h);
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const cplx<T>* sl = spec + (q0 + b) * SLOT + c;
@@ -148,7 +168,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 static_for<0, N2>([&](auto kc) { v[b][q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
             });
         });
-        __syncthreads();
+        group_sync<NT, G>(h);
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             cplx<T>* sl = own + (q0 + b) * SLOT;
@@ -192,6 +212,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 });
             });
         }
+        drain();
         return;
     }
 
@@ -203,7 +224,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
             const cplx<T>* sl = own + (q0 + b) * SLOT;
             static_for<0, N1>([&](auto rc) { v[b][decltype(rc)::value] = sl[decltype(rc)::value * RP]; });
         });
-        __syncthreads();
+        group_sync<NT, G>(h);
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             cplx<T>* sl = spec + (q0 + b) * SLOT + c;
@@ -226,7 +247,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 });
             });
         });
-        __syncthreads();
+        group_sync<NT, G>(h);
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const cplx<T>* sl = own + (q0 + b) * SLOT;
@@ -239,6 +260,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
             static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
         });
     }
+    drain();
 }
 
 // Two thread groups per block (each transforms three components; the update

@@ -52,7 +52,6 @@ constexpr int kRcThreads = 256;
 constexpr int kRcC = 8;               // blocks per plane (cluster size)
 constexpr int kM = 128;               // complex elements per row
 constexpr int kNy = 256;
-
 // tile [256][16]
 __device__ __forceinline__ int sw16(int row, int col) { return row * 16 + (col ^ (row & 15)); }
 
@@ -85,42 +84,35 @@ __device__ __forceinline__ void c2r_pair(float2 X, float2 P, float2 w, float2* a
     *b = make_float2(Pp.x + U.y, U.x - Pp.y);         // conj(Pp - i U)
 }
 
-__global__ void __launch_bounds__(kRcThreads)
-plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
-                 float2* __restrict__ nyq) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* tile = reinterpret_cast<float2*>(smem_raw);
-    __shared__ float2 col0[kNy];                       // block 0: the packed column after the y transform
+// ---------------------------------------------------------------------------
+// Phases of one plane.
 
-    pdl_launch_dependents();
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster.barrier_arrive();                          // wait for all blocks before the first remote store
-    const int r = (int)cluster.block_rank();
-    float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
-    const int tid = threadIdx.x;
-    pdl_wait();
+// r2c phase 1 compute: stage A over n1 of the row segment in v (lane j holds
+// z[j + 8 n1]) and the twiddles W_128^{j k1}.
+__device__ __forceinline__ void r2c_stage_a(float2 (&v)[16], int j, const float2* __restrict__ twx) {
+    reg_dft<float, -1, 16>(v);
+    static_for<1, 16>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        if (j) v[k1] = cmul(v[k1], twx[2 * j * k1]);
+    });
+}
 
-    // ---------------- phase 1: stage A of rows 32 r .. 32 r + 31, scatter by k1
-    {
-        const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
-        const int y = 32 * r + w + 8 * g;              // rows of a warp alternate in bit 3 (bank spread)
-        const float2* p = plane + (size_t)y * kM;
-        float2 v[16];
-        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = p[j + 8 * decltype(nc)::value]; });
-        reg_dft<float, -1, 16>(v);
-        static_for<1, 16>([&](auto kc) {
-            constexpr int k1 = decltype(kc)::value;
-            if (j) v[k1] = cmul(v[k1], twx[2 * j * k1]);
-        });
-        cluster.barrier_wait();
-        static_for<0, 16>([&](auto kc) {
-            constexpr int k1 = decltype(kc)::value;
-            float2* dst = cluster.map_shared_rank(tile, owner_of(k1));
-            dst[sw16(y, half_of(k1) * 8 + j)] = v[k1];
-        });
-    }
-    cluster.sync();
+// r2c phase 1 exchange: row y's outputs k1 to the block that owns k1.
+__device__ __forceinline__ void r2c_scatter(const float2 (&v)[16], cg::cluster_group& cluster, float2* tile, int y,
+                                            int j) {
+    static_for<0, 16>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        float2* dst = cluster.map_shared_rank(tile, owner_of(k1));
+        dst[sw16(y, half_of(k1) * 8 + j)] = v[k1];
+    });
+}
 
+// r2c phases 2a and 2b on the block's 16 columns (the tile holds the
+// exchanged stage-A outputs), spectra stored to `plane`, block 0's x Nyquist
+// column to nq.
+__device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, int tid, const float2* __restrict__ twx,
+                                            const float2* __restrict__ twy, float2* __restrict__ plane,
+                                            float2* __restrict__ nq) {
     // ---------------- phase 2a: stage B and the r2c pairing, one row per thread
     {
         const int y = tid;
@@ -130,26 +122,27 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
             static_for<0, 8>([&](auto jc) { a[s][decltype(jc)::value] = tile[sw16(y, s * 8 + decltype(jc)::value)]; });
             reg_dft<float, -1, 8>(a[s]);               // a[s][k2] = Z[k1(r, s) + 16 k2]
         });
-        float2 o[2][8];
+        // the pairing is done in place: each pair (k, 128 - k) is read and
+        // written at the same two registers
         if (r == 0) {
-            o[0][0] = make_float2(a[0][0].x + a[0][0].y, a[0][0].x - a[0][0].y);   // X[0] + i X[128]
+            a[0][0] = make_float2(a[0][0].x + a[0][0].y, a[0][0].x - a[0][0].y);   // X[0] + i X[128]
             static_for<1, 5>([&](auto kc) {            // k = 16 k2 pairs with 16 (8 - k2)
                 constexpr int k2 = decltype(kc)::value;
-                r2c_pair(a[0][k2], a[0][8 - k2], w256<16 * k2>(), &o[0][k2], &o[0][8 - k2]);
+                r2c_pair(a[0][k2], a[0][8 - k2], w256<16 * k2>(), &a[0][k2], &a[0][8 - k2]);
             });
             static_for<0, 4>([&](auto kc) {            // k = 8 + 16 k2 pairs with 8 + 16 (7 - k2)
                 constexpr int k2 = decltype(kc)::value;
-                r2c_pair(a[1][k2], a[1][7 - k2], w256<8 + 16 * k2>(), &o[1][k2], &o[1][7 - k2]);
+                r2c_pair(a[1][k2], a[1][7 - k2], w256<8 + 16 * k2>(), &a[1][k2], &a[1][7 - k2]);
             });
         } else {
             static_for<0, 8>([&](auto kc) {            // k = r + 16 k2 pairs with (16 - r) + 16 (7 - k2)
                 constexpr int k2 = decltype(kc)::value;
-                r2c_pair(a[0][k2], a[1][7 - k2], twx[r + 16 * k2], &o[0][k2], &o[1][7 - k2]);
+                r2c_pair(a[0][k2], a[1][7 - k2], twx[r + 16 * k2], &a[0][k2], &a[1][7 - k2]);
             });
         }
         static_for<0, 2>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            static_for<0, 8>([&](auto kc) { tile[sw16(y, s * 8 + decltype(kc)::value)] = o[s][decltype(kc)::value]; });
+            static_for<0, 8>([&](auto kc) { tile[sw16(y, s * 8 + decltype(kc)::value)] = a[s][decltype(kc)::value]; });
         });
     }
     __syncthreads();
@@ -169,7 +162,6 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
             if (c == 0) static_for<0, 16>([&](auto kc) { col0[jy + 16 * decltype(kc)::value] = v[decltype(kc)::value]; });
             __syncthreads();
             if (c == 0) {
-                float2* nq = nyq + (size_t)(blockIdx.x / kRcC) * kNy;
                 static_for<0, 16>([&](auto kc) {
                     constexpr int k2 = decltype(kc)::value;
                     const int ky = jy + 16 * k2;
@@ -187,7 +179,131 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     }
 }
 
+// c2r phase 1: inverse y on the block's slots from v (thread (c, jy) holds
+// slot 16 r + c at rows jy + 16 k2), block 0 repacks slot 0 as S0 + i SN first;
+// the column results end in the tile as [row][column].
+__device__ __forceinline__ void c2r_columns(float2 (&v)[16], float2* tile, int r, int c, int jy,
+                                            const float2* __restrict__ twy, const float2* __restrict__ nq) {
+    if (r == 0 && c == 0) {                            // repack slot 0: S0 + i SN
+        static_for<0, 16>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            const float2 sn = nq[jy + 16 * k2];
+            v[k2] = make_float2(v[k2].x - sn.y, v[k2].y + sn.x);
+        });
+    }
+    reg_dft<float, +1, 16>(v);                         // over k2, k1 = jy
+    static_for<0, 16>([&](auto nc) {
+        constexpr int n2 = decltype(nc)::value;
+        float2 val = v[n2];
+        if (n2 > 0 && jy > 0) val = cmulc(val, twy[n2 * jy]);
+        tile[sw16(16 * jy + n2, c)] = val;              // element (k1 = jy, n2)
+    });
+    __syncthreads();
+    static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[sw16(16 * decltype(kc)::value + jy, c)]; });
+    reg_dft<float, +1, 16>(v);                         // v[n1] = y[jy + 16 n1]
+    static_for<0, 16>([&](auto nc) { tile[sw16(jy + 16 * decltype(nc)::value, c)] = v[decltype(nc)::value]; });
+}
+
+// c2r phase 1b: c2r pairing and inverse stage B of row y = tid, then the
+// exchange of the rows to their owners (arrives on and waits for the cluster
+// barrier that frees every block's tile).
+__device__ __forceinline__ void c2r_rows(float2* tile, cg::cluster_group& cluster, int r, int tid,
+                                         const float2* __restrict__ twx) {
+    const int y = tid;
+    float2 x[2][8];
+    static_for<0, 2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<0, 8>([&](auto kc) { x[s][decltype(kc)::value] = tile[sw16(y, s * 8 + decltype(kc)::value)]; });
+    });
+    cluster.barrier_arrive();                          // this block's tile is free for the remote stores
+    float2 z[2][8];
+    if (r == 0) {
+        z[0][0] = make_float2(x[0][0].x + x[0][0].y, x[0][0].x - x[0][0].y);   // X[0] = re, X[128] = im
+        static_for<1, 5>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            c2r_pair(x[0][k2], x[0][8 - k2], w256<16 * k2>(), &z[0][k2], &z[0][8 - k2]);
+        });
+        static_for<0, 4>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            c2r_pair(x[1][k2], x[1][7 - k2], w256<8 + 16 * k2>(), &z[1][k2], &z[1][7 - k2]);
+        });
+    } else {
+        static_for<0, 8>([&](auto kc) {
+            constexpr int k2 = decltype(kc)::value;
+            c2r_pair(x[0][k2], x[1][7 - k2], twx[r + 16 * k2], &z[0][k2], &z[1][7 - k2]);
+        });
+    }
+    const int k1s[2] = {r == 0 ? 0 : r, r == 0 ? 8 : 16 - r};
+    static_for<0, 2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        reg_dft<float, +1, 8>(z[s]);                   // over k2 -> j
+        const int k1 = k1s[s];
+        static_for<1, 8>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            if (k1) z[s][j] = cmulc(z[s][j], twx[2 * j * k1]);
+        });
+    });
+    cluster.barrier_wait();
+    // row y goes to block y / 32; element (k1, j) of local row yl at k1 * 256 + j * 32 + (yl ^ j):
+    // the warp's 32 rows fill one contiguous 256-byte block per store
+    const int yl = y & 31;
+    float2* dst = cluster.map_shared_rank(tile, y >> 5);
+    static_for<0, 2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<0, 8>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            dst[k1s[s] * 256 + j * 32 + (yl ^ j)] = z[s][j];
+        });
+    });
+}
+
+// c2r phase 3: inverse stage A of the block's rows 32 r .. 32 r + 31, stored.
+__device__ __forceinline__ void c2r_stage_a_store(const float2* tile, int r, int tid, float2* __restrict__ plane) {
+    const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
+    const int yl = w + 8 * g;
+    float2 v[16];
+    static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[decltype(kc)::value * 256 + j * 32 + (yl ^ j)]; });
+    reg_dft<float, +1, 16>(v);                         // v[n1] = z[j + 8 n1]
+    float2* p = plane + (size_t)(32 * r + yl) * kM;
+    static_for<0, 16>([&](auto nc) { p[j + 8 * decltype(nc)::value] = v[decltype(nc)::value]; });
+}
+
+constexpr size_t kTileBytes = (size_t)kM * kNy / kRcC * sizeof(float2);   // 32 KB
+
+// 64 registers: four blocks per SM
 __global__ void __launch_bounds__(kRcThreads)
+plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
+                 float2* __restrict__ nyq) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+    __shared__ float2 col0[kNy];                       // block 0: the packed column after the y transform
+
+    pdl_launch_dependents();
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.barrier_arrive();                          // wait for all blocks before the first remote store
+    const int r = (int)cluster.block_rank();
+    const int pl = blockIdx.x / kRcC;
+    float2* plane = data + (size_t)pl * (kM * kNy);
+    const int tid = threadIdx.x;
+    pdl_wait();
+
+    {
+        const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
+        const int y = 32 * r + w + 8 * g;              // rows of a warp alternate in bit 3 (bank spread)
+        const float2* p = plane + (size_t)y * kM;
+        float2 v[16];
+        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = p[j + 8 * decltype(nc)::value]; });
+        r2c_stage_a(v, j, twx);
+        cluster.barrier_wait();
+        r2c_scatter(v, cluster, tile, y, j);
+    }
+    cluster.sync();
+    r2c_columns(tile, col0, r, tid, twx, twy, plane, nyq + (size_t)pl * kNy);
+}
+
+// capped at 48 registers: five blocks per SM (the packed butterfly adds would
+// otherwise take it to 54 registers and four blocks)
+__global__ void __launch_bounds__(kRcThreads, 5)
 plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
                  const float2* __restrict__ nyq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -196,99 +312,22 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     pdl_launch_dependents();
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
-    float2* plane = data + (size_t)(blockIdx.x / kRcC) * (kM * kNy);
+    const int pl = blockIdx.x / kRcC;
+    float2* plane = data + (size_t)pl * (kM * kNy);
     const int tid = threadIdx.x;
     pdl_wait();
 
-    // ---------------- phase 1: inverse y on slots 16 r .. 16 r + 15
     {
         const int c = tid & 15, jy = tid >> 4;
         const float2* in = plane + 16 * r + c;
         float2 v[16];
         static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = in[(size_t)(jy + 16 * decltype(kc)::value) * kM]; });
-        if (r == 0 && c == 0) {                        // repack slot 0: S0 + i SN
-            const float2* nq = nyq + (size_t)(blockIdx.x / kRcC) * kNy;
-            static_for<0, 16>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                const float2 sn = nq[jy + 16 * k2];
-                v[k2] = make_float2(v[k2].x - sn.y, v[k2].y + sn.x);
-            });
-        }
-        reg_dft<float, +1, 16>(v);                     // over k2, k1 = jy
-        static_for<0, 16>([&](auto nc) {
-            constexpr int n2 = decltype(nc)::value;
-            float2 val = v[n2];
-            if (n2 > 0 && jy > 0) val = cmulc(val, twy[n2 * jy]);
-            tile[sw16(16 * jy + n2, c)] = val;          // element (k1 = jy, n2)
-        });
-        __syncthreads();
-        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[sw16(16 * decltype(kc)::value + jy, c)]; });
-        reg_dft<float, +1, 16>(v);                     // v[n1] = y[jy + 16 n1]
-        static_for<0, 16>([&](auto nc) { tile[sw16(jy + 16 * decltype(nc)::value, c)] = v[decltype(nc)::value]; });
+        c2r_columns(v, tile, r, c, jy, twy, nyq + (size_t)pl * kNy);
     }
     __syncthreads();
-
-    // ---------------- phase 1b: c2r pairing and inverse stage B, one row per thread
-    {
-        const int y = tid;
-        float2 x[2][8];
-        static_for<0, 2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<0, 8>([&](auto kc) { x[s][decltype(kc)::value] = tile[sw16(y, s * 8 + decltype(kc)::value)]; });
-        });
-        cluster.barrier_arrive();                      // this block's tile is free for the remote stores
-        float2 z[2][8];
-        if (r == 0) {
-            z[0][0] = make_float2(x[0][0].x + x[0][0].y, x[0][0].x - x[0][0].y);   // X[0] = re, X[128] = im
-            static_for<1, 5>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                c2r_pair(x[0][k2], x[0][8 - k2], w256<16 * k2>(), &z[0][k2], &z[0][8 - k2]);
-            });
-            static_for<0, 4>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                c2r_pair(x[1][k2], x[1][7 - k2], w256<8 + 16 * k2>(), &z[1][k2], &z[1][7 - k2]);
-            });
-        } else {
-            static_for<0, 8>([&](auto kc) {
-                constexpr int k2 = decltype(kc)::value;
-                c2r_pair(x[0][k2], x[1][7 - k2], twx[r + 16 * k2], &z[0][k2], &z[1][7 - k2]);
-            });
-        }
-        const int k1s[2] = {r == 0 ? 0 : r, r == 0 ? 8 : 16 - r};
-        static_for<0, 2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            reg_dft<float, +1, 8>(z[s]);               // over k2 -> j
-            const int k1 = k1s[s];
-            static_for<1, 8>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                if (k1) z[s][j] = cmulc(z[s][j], twx[2 * j * k1]);
-            });
-        });
-        cluster.barrier_wait();
-        // row y goes to block y / 32; element (k1, j) of local row yl at k1 * 256 + j * 32 + (yl ^ j):
-        // the warp's 32 rows fill one contiguous 256-byte block per store
-        float2* dst = cluster.map_shared_rank(tile, y >> 5);
-        const int yl = y & 31;
-        static_for<0, 2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<0, 8>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                dst[k1s[s] * 256 + j * 32 + (yl ^ j)] = z[s][j];
-            });
-        });
-    }
+    c2r_rows(tile, cluster, r, tid, twx);
     cluster.sync();
-
-    // ---------------- phase 3: inverse stage A of rows 32 r .. 32 r + 31
-    {
-        const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
-        const int yl = w + 8 * g;
-        float2 v[16];
-        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[decltype(kc)::value * 256 + j * 32 + (yl ^ j)]; });
-        reg_dft<float, +1, 16>(v);                     // v[n1] = z[j + 8 n1]
-        float2* p = plane + (size_t)(32 * r + yl) * kM;
-        static_for<0, 16>([&](auto nc) { p[j + 8 * decltype(nc)::value] = v[decltype(nc)::value]; });
-    }
+    c2r_stage_a_store(tile, r, tid, plane);
 }
 
 }  // namespace
@@ -300,11 +339,10 @@ bool plane_rc_supported(int prec, const GridGeom& g) { return prec == 32 && g.Nx
 cudaError_t launch_plane_rc(float* data, float2* nyq, int ncomp, const GridGeom& g, const Tables<float>& tb, int dir,
                             cudaStream_t s) {
     if (!plane_rc_supported(32, g)) return cudaErrorNotSupported;
-    const size_t smem = (size_t)kM * kNy / kRcC * sizeof(float2);    // 32 KB
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((long long)ncomp * g.Nz * kRcC), 1, 1);
     cfg.blockDim = dim3(kRcThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = kTileBytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -496,12 +496,12 @@ cudaError_t spectral_pass_real(psatd_ctx* c) {
     const Tables<float> tb = tables<float>(c);
     float* f = static_cast<float*>(c->fields);
     float2* nyq = static_cast<float2*>(c->nyq.p);
+    if (!ensure_field_map(c) || !c->nyq_map_ok) return cudaErrorNotSupported;
     cudaError_t e = timed(c, PSATD_KERNEL_PLANE_XY, [&] {
         ++c->launches;
         return launch_plane_rc(f, nyq, 6, g, tb, -1, c->stream);
     });
     if (e != cudaSuccess) return e;
-    if (!ensure_field_map(c) || !c->nyq_map_ok) return cudaErrorNotSupported;
     const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p),
                               static_cast<const ModeCoef<float>*>(c->slot_coef.p), nyq, &c->nyq_map};
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
