@@ -48,7 +48,7 @@ typedef enum psatd_status {
     PSATD_ERR_STATE = -6     /* call not valid in the current state (e.g. no fields) */
 } psatd_status;
 
-enum { PSATD_PULSE_FLAT_TOP = 0, PSATD_PULSE_GAUSSIAN = 1 };
+enum { PSATD_PULSE_FLAT_TOP = 0, PSATD_PULSE_GAUSSIAN = 1, PSATD_PULSE_PROFILE = 2 };
 enum { PSATD_FORWARD = -1, PSATD_INVERSE = +1 };
 enum { PSATD_FLAG_NO_FIELD_ALLOC = 1,     /* init_grid: caller binds field storage */
        PSATD_FLAG_REAL_FIELDS = 2 };     /* init_grid: real field storage (see below) */
@@ -78,7 +78,7 @@ typedef struct psatd_mapping {
  * E = u_phi s0(d1) + e u_{phi+pi/2} s0(d2) and likewise B with s1.  Replicas of the
  * pulse spaced D along x are summed at every node (Sec. 2.3). */
 typedef struct psatd_pulse {
-    int kind;            /* PSATD_PULSE_FLAT_TOP or PSATD_PULSE_GAUSSIAN */
+    int kind;            /* PSATD_PULSE_FLAT_TOP, PSATD_PULSE_GAUSSIAN or PSATD_PULSE_PROFILE */
     int div_project;     /* nonzero: remove k^(k^.E) and k^(k^.B) once after init (Sec. 2.1) */
     double lambda;       /* carrier wavelength */
     double theta;        /* flat-top half angle theta; Gaussian theta0 */
@@ -155,6 +155,22 @@ psatd_status psatd_get_field(psatd_ctx* ctx, int comp, void* dst, int dst_on_dev
  * Sec. 3.2.1).  Coordinates and the pulse are evaluated in float64 and rounded
  * once.  Resets the time to 0. */
 psatd_status psatd_init_pulse(psatd_ctx* ctx, const psatd_pulse* pulse);
+
+/* Longitudinal profile of PSATD_PULSE_PROFILE pulses.  Sec. 2.2 lets the pulse
+ * have an arbitrary profile along the radial direction; this kind keeps the
+ * flat-top transverse shape of Eq. 5 and the amplitude A/R of Eq. 8-9, and takes
+ * the longitudinal factor from a table: u_l(zeta) = Re(a(zeta) e^{i phi}) with
+ * zeta = R - R0, phi the pulse's cep (cep + pi/2 for the second polarisation)
+ * and a(zeta) the complex (analytic) waveform linearly interpolated between the
+ * samples a_k = a(zeta0 + k dzeta), k < n; u_l = 0 outside [zeta0, zeta0 +
+ * (n-1) dzeta] and outside |zeta| <= L/2.  With a the analytic signal g + i H[g]
+ * of a real waveform g (H the Hilbert transform along zeta), phi acts as a
+ * carrier-envelope phase: a = -i e^{i k zeta} cos^2(pi zeta/L) gives Eq. 7's
+ * sin(k zeta + phi) cos^2(pi zeta/L).
+ * samples: 2n float64 (re, im interleaved), host memory, copied; n in
+ * 2..1048576, dzeta > 0, all finite.  The table stays with the context until
+ * replaced.  Synchronises. */
+psatd_status psatd_set_pulse_profile(psatd_ctx* ctx, const double* samples, int n, double zeta0, double dzeta);
 
 /* Advance n_steps >= 0 PSATD steps of size dt (Eq. 3-4): per step a forward 3D
  * FFT of the six components, the per-mode update, and an inverse 3D FFT; the

@@ -34,6 +34,10 @@ design notes):
       planes, where the wave number -pi/d is its own mirror index; the real
       part there is the mean of the update at kappa and at kappa with its
       Nyquist components negated.
+  R21 tabulated longitudinal profile (Sec. 2.2 allows any profile along the
+      radial direction): Eq. 8 with the flat-top transverse shape of Eq. 5 and
+      the amplitude A of Eq. 9, u_l(zeta) = Re(a(zeta) e^{i phi}) with a the
+      analytic waveform linearly interpolated between given samples.
 """
 from __future__ import annotations
 
@@ -43,7 +47,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "Grid", "Mapping", "Pulse", "FLAT_TOP", "GAUSSIAN",
+    "Grid", "Mapping", "Pulse", "FLAT_TOP", "GAUSSIAN", "PROFILE", "profile_ul",
     "wavenumbers", "fft3", "ifft3", "dft3_naive", "idft3_naive",
     "psatd_update", "psatd_step", "advance", "advance_exact",
     "psatd_step_real", "advance_real",
@@ -56,6 +60,7 @@ __all__ = [
 
 FLAT_TOP = 0
 GAUSSIAN = 1
+PROFILE = 2
 
 
 # ----------------------------------------------------------------------------
@@ -115,6 +120,11 @@ class Pulse:
     ellipticity: float = 0.0  # e (R13)
     pol_angle: float = 0.0    # psi (R13): d1 = (0, cos psi, sin psi)
     div_project: int = 0      # one-time transverse projection after init (R4)
+    # PROFILE (R21): complex samples a_k = a(profile_z0 + k profile_dz) of the
+    # longitudinal waveform
+    profile: np.ndarray | None = None
+    profile_z0: float = 0.0
+    profile_dz: float = 1.0
 
 
 # ----------------------------------------------------------------------------
@@ -281,6 +291,18 @@ def u_l_flat(s, lam: float, L: float, phase: float = 0.0):
     return np.sin(2 * np.pi * s / lam + phase) * np.cos(np.pi * s / L) ** 2 * omega(s, -L / 2, L / 2)
 
 
+def profile_ul(s, a, z0: float, dz: float, phase: float = 0.0):
+    """Tabulated longitudinal factor Re(a(s) e^{i phase}) (R21): the samples
+    a_k = a(z0 + k dz) joined by straight lines, zero outside [z0, z0 + (n-1) dz]."""
+    s = np.asarray(s, dtype=np.float64)
+    a = np.asarray(a, dtype=np.complex128)
+    zk = z0 + dz * np.arange(a.size)
+    inside = (s >= z0) & (s <= zk[-1])
+    ar = np.interp(s, zk, a.real)
+    ai = np.interp(s, zk, a.imag)
+    return np.where(inside, ar * math.cos(phase) - ai * math.sin(phase), 0.0)
+
+
 def flat_top_A(P0: float, c: float, theta: float) -> float:
     """Amplitude of Eq. 9, A = sqrt(4 P0 / (c (1 - cos theta)))."""
     return math.sqrt(4.0 * P0 / (c * (1.0 - math.cos(theta))))
@@ -320,6 +342,7 @@ def pulse_scalar(X, Y, Z, pulse: Pulse, mapping: Mapping, c: float, phase: float
 
     FLAT_TOP: Eq. 8, u = A/R * u_l(R - R0) * u_ts(alpha).
     GAUSSIAN: Sec. 3.2.1 with R12, u = E0 R0 sin(k(R-R0)+phase) u_l u_ts / R.
+    PROFILE: Eq. 8 with the tabulated u_l of R21 on |R - R0| <= L/2.
     """
     R = np.sqrt(X * X + Y * Y + Z * Z)
     Rs = np.where(R > 0, R, 1.0)
@@ -328,6 +351,11 @@ def pulse_scalar(X, Y, Z, pulse: Pulse, mapping: Mapping, c: float, phase: float
     if pulse.kind == FLAT_TOP:
         A = flat_top_A(pulse.P0, c, pulse.theta)
         u = A / Rs * u_l_flat(zeta, pulse.lam, mapping.L, phase) * u_ts_flat(alpha, pulse.theta, pulse.eps)
+    elif pulse.kind == PROFILE:
+        A = flat_top_A(pulse.P0, c, pulse.theta)
+        ul = profile_ul(zeta, pulse.profile, pulse.profile_z0, pulse.profile_dz, phase) \
+            * omega(zeta, -mapping.L / 2, mapping.L / 2)
+        u = A / Rs * ul * u_ts_flat(alpha, pulse.theta, pulse.eps)
     elif pulse.kind == GAUSSIAN:
         E0 = gaussian_E0(pulse.P0, c, mapping.R0, pulse.theta)
         k = 2 * np.pi / pulse.lam

@@ -90,7 +90,10 @@ struct ShellGeom { double R0, L; };
 struct PulseParams {
     int kind, div_project;
     double lambda, theta, eps, P0, n_cycles, cep, ellipticity, pol_angle;
-    double amp;          // A (flat-top) or E0 (Gaussian), computed on the host
+    double amp;          // A (flat-top, profile) or E0 (Gaussian), computed on the host
+    const double2* prof; // profile kind: complex samples a_k = a(prof_z0 + k prof_dz), k < prof_n
+    int prof_n;
+    double prof_z0, prof_dz;
 };
 
 // Device tables of one context.

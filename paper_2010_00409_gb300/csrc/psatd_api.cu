@@ -94,6 +94,11 @@ struct psatd_ctx {
     DevBuf tw[3], k[3], coef;
     AxisPlan plan[3];
 
+    // longitudinal profile of PSATD_PULSE_PROFILE pulses (psatd_set_pulse_profile)
+    DevBuf lprof;
+    int lprof_n = 0;
+    double lprof_z0 = 0.0, lprof_dz = 0.0;
+
     // scratch (device), allocated on first use
     DevBuf diag_spec, diag_partial, diag_out;
     DevBuf samp_wx, samp_wy, samp_wz, samp_g, samp_h, samp_out;
@@ -716,6 +721,7 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef_proj);
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
+    free_buf(c->lprof);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
     for (auto& p : c->pending) { c->ev_pool.push_back(p.a); c->ev_pool.push_back(p.b); }
@@ -731,6 +737,25 @@ psatd_status psatd_set_dt(psatd_ctx* c, double dt) {
     st = set_coef(c, dt);
     if (st == PSATD_OK) c->dt = dt;
     return st;
+}
+
+psatd_status psatd_set_pulse_profile(psatd_ctx* c, const double* samples, int n, double zeta0, double dzeta) {
+    psatd_status st = check_ctx(c, false);
+    if (st) return st;
+    if (!samples) return fail(c, PSATD_ERR_ARG, "NULL profile samples");
+    if (n < 2 || n > (1 << 20)) return fail(c, PSATD_ERR_ARG, "profile needs 2 <= n <= 1048576 samples");
+    if (!is_finite(zeta0) || !is_finite(dzeta) || !(dzeta > 0))
+        return fail(c, PSATD_ERR_ARG, "profile needs finite zeta0 and dzeta > 0");
+    for (int i = 0; i < 2 * n; ++i)
+        if (!is_finite(samples[i])) return fail(c, PSATD_ERR_ARG, "profile samples must be finite");
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "psatd_set_pulse_profile cannot be captured in a batch");
+    CK(c, cudaStreamSynchronize(c->stream));           // a previous table may still be read
+    CK(c, ensure_buf(c->lprof, (size_t)n * sizeof(double2)));
+    CK(c, cudaMemcpy(c->lprof.p, samples, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice));
+    c->lprof_n = n;
+    c->lprof_z0 = zeta0;
+    c->lprof_dz = dzeta;
+    return PSATD_OK;
 }
 
 psatd_status psatd_set_mapping(psatd_ctx* c, const psatd_mapping* m) {
@@ -816,8 +841,10 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
         return PSATD_OK;
     }
     if (!p) return fail(c, PSATD_ERR_ARG, "NULL pulse");
-    if (p->kind != PSATD_PULSE_FLAT_TOP && p->kind != PSATD_PULSE_GAUSSIAN)
+    if (p->kind != PSATD_PULSE_FLAT_TOP && p->kind != PSATD_PULSE_GAUSSIAN && p->kind != PSATD_PULSE_PROFILE)
         return fail(c, PSATD_ERR_ARG, "unknown pulse kind");
+    if (p->kind == PSATD_PULSE_PROFILE && c->lprof_n < 2)
+        return fail(c, PSATD_ERR_STATE, "a profile pulse needs psatd_set_pulse_profile first");
     const double vals[8] = {p->lambda, p->theta, p->eps, p->P0, p->n_cycles, p->cep, p->ellipticity, p->pol_angle};
     for (double v : vals)
         if (!is_finite(v)) return fail(c, PSATD_ERR_ARG, "pulse parameters must be finite");
@@ -827,7 +854,7 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
         return fail(c, PSATD_ERR_ARG, "Gaussian pulse needs n_cycles > 0");
     if (!(c->mapping.R0 > 0) || !(c->mapping.L > 0))
         return fail(c, PSATD_ERR_ARG, "mapping R0 and L must be > 0 for a pulse");
-    if (p->kind == PSATD_PULSE_FLAT_TOP && !(std::cos(p->theta) < 1.0))
+    if (p->kind != PSATD_PULSE_GAUSSIAN && !(std::cos(p->theta) < 1.0))
         return fail(c, PSATD_ERR_ARG, "flat-top theta too small");
 
     PulseParams pp;
@@ -835,7 +862,11 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
     pp.lambda = p->lambda; pp.theta = p->theta; pp.eps = p->eps; pp.P0 = p->P0;
     pp.n_cycles = p->n_cycles; pp.cep = p->cep; pp.ellipticity = p->ellipticity;
     pp.pol_angle = p->pol_angle;
-    if (p->kind == PSATD_PULSE_FLAT_TOP)
+    pp.prof = static_cast<const double2*>(c->lprof.p);
+    pp.prof_n = c->lprof_n;
+    pp.prof_z0 = c->lprof_z0;
+    pp.prof_dz = c->lprof_dz;
+    if (p->kind != PSATD_PULSE_GAUSSIAN)
         pp.amp = std::sqrt(4.0 * p->P0 / (c->grid.c * (1.0 - std::cos(p->theta))));           // Eq. 9
     else
         pp.amp = std::sqrt(4.0 * p->P0 / (c->grid.c * c->mapping.R0 * c->mapping.R0 * F_series(p->theta)));

@@ -27,6 +27,19 @@ __device__ __forceinline__ double u_ts_flat(double a, double th, double eps) {
     return 0.0;
 }
 
+// Tabulated longitudinal factor Re(a(zeta) e^{i phase}), a linearly
+// interpolated between the samples; 0 outside the table.
+__device__ __forceinline__ double profile_ul(double zeta, const PulseParams& p, double phase) {
+    const double s = (zeta - p.prof_z0) / p.prof_dz;
+    if (!(s >= 0.0) || s > (double)(p.prof_n - 1)) return 0.0;
+    int k = (int)s;
+    if (k > p.prof_n - 2) k = p.prof_n - 2;
+    const double t = s - k;
+    const double2 a0 = p.prof[k], a1 = p.prof[k + 1];
+    const double ar = a0.x + t * (a1.x - a0.x), ai = a0.y + t * (a1.y - a0.y);
+    return ar * cos(phase) - ai * sin(phase);
+}
+
 // Scalar amplitude u(R) with carrier phase `phase`; 0 outside the support.
 __device__ __forceinline__ double pulse_u(double X, double Y, double Z, const PulseParams& p,
                                           const ShellGeom& sh, double phase) {
@@ -42,6 +55,12 @@ __device__ __forceinline__ double pulse_u(double X, double Y, double Z, const Pu
         const double cl = cos(kPi * zeta / sh.L);
         const double ul = sin(2.0 * kPi * zeta / p.lambda + phase) * cl * cl;
         return p.amp / R * ul * uts;
+    }
+    if (p.kind == 2) {
+        // flat-top transverse shape (Eq. 5), tabulated longitudinal profile
+        const double uts = u_ts_flat(alpha, p.theta, p.eps);
+        if (uts == 0.0) return 0.0;
+        return p.amp / R * profile_ul(zeta, p, phase) * uts;
     }
     // Gaussian, Sec. 3.2.1
     double uts = u_ts_flat(alpha, 2.0 * p.theta, p.eps);
@@ -86,6 +105,13 @@ __device__ __forceinline__ float pulse_u_f(double X, double Y, double Z, const P
     const double zeta = R - sh.R0;
     if (zeta < -0.5 * sh.L || zeta > 0.5 * sh.L) return 0.f;
     const float alpha = atan2f(sqrtf((float)(Y * Y + Z * Z)), (float)(-X));
+    if (p.kind == 2) {
+        // tabulated profile: the interpolation in float64 (a sample spacing of a
+        // few nm against |zeta| of tens of um), the transverse shape in float32
+        const float uts = u_ts_flat_f(alpha, (float)p.theta, (float)p.eps);
+        if (uts == 0.f) return 0.f;
+        return (float)(p.amp / R * profile_ul(zeta, p, phase)) * uts;
+    }
     const double arg = 2.0 * kPi * zeta / p.lambda + phase;
     const float carrier = sinf((float)(arg - 2.0 * kPi * rint(arg / (2.0 * kPi))));
     const float zf = (float)zeta;

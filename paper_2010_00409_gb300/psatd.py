@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libpsatd.so")
 
 OK = 0
 ERR_ARG, ERR_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6
-FLAT_TOP, GAUSSIAN = 0, 1
+FLAT_TOP, GAUSSIAN, PROFILE = 0, 1, 2
 FORWARD, INVERSE = -1, +1
 FLAG_NO_FIELD_ALLOC = 1
 FLAG_REAL_FIELDS = 2
@@ -33,7 +33,7 @@ EXPORTS = (
     "psatd_batch_nodes", "psatd_batch_destroy", "psatd_autotune",
     "psatd_fno_create", "psatd_fno_destroy", "psatd_fno_num_params", "psatd_fno_buffers", "psatd_fno_forward",
     "psatd_fno_loss_backward", "psatd_fno_adam_step", "psatd_fno_synchronize", "psatd_fno_last_error",
-    "psatd_gemm_bf16", "psatd_set_mapping",
+    "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_set_field": (C.c_int, [P, C.c_int, P, C.c_int]),
         "psatd_get_field": (C.c_int, [P, C.c_int, P, C.c_int]),
         "psatd_init_pulse": (C.c_int, [P, C.POINTER(PsatdPulse)]),
+        "psatd_set_pulse_profile": (C.c_int, [P, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_double]),
         "psatd_advance": (C.c_int, [P, C.c_int]),
         "psatd_fft": (C.c_int, [P, C.c_int]),
         "psatd_sample_focal_plane": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -374,6 +375,13 @@ class Context:
         out = np.empty(((6,) if comp < 0 else ()) + shape, dtype=self._np_field)
         _check(lib().psatd_get_field(self._ptr, comp, out.ctypes.data_as(C.c_void_p), 0), self._ptr)
         return out
+
+    def set_pulse_profile(self, a, zeta0: float, dzeta: float):
+        """Longitudinal profile of PROFILE pulses: complex samples a_k = a(zeta0 + k dzeta)."""
+        z = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+        buf = z.view(np.float64)
+        _check(lib().psatd_set_pulse_profile(self._ptr, buf.ctypes.data_as(C.POINTER(C.c_double)), int(z.size),
+                                             float(zeta0), float(dzeta)), self._ptr)
 
     def init_pulse(self, pulse):
         _check(lib().psatd_init_pulse(self._ptr, C.byref(make_pulse(pulse))), self._ptr)

@@ -222,3 +222,88 @@ def batched_sweep(n: int = 64, seed: int = 0, lam: float = LAMBDA0):
         plane = dict(x_p=0.0, ny=64, nz=64, y0=-1.5 * lam, y1=1.5 * lam, z0=-1.5 * lam, z1=1.5 * lam)
         out.append((g, MappingSpec(R0, L), p, R0 / C_CGS, plane))
     return out
+
+
+# --------------------------------------------------------------------------
+# Multi-octave workload: 400-3200 nm spectrum, seeded GDD / TOD, f = 0.5,
+# tabulated longitudinal profile on a mapped grid (1024^3 at full size)
+# --------------------------------------------------------------------------
+PROFILE = 2
+MO_LAM_MIN = 400e-7            # cm
+MO_LAM_MAX = 3200e-7           # cm
+MO_GDD_FS2 = 2.0               # |GDD| bound, fs^2
+MO_TOD_FS3 = 4.0               # |TOD| bound, fs^3
+
+
+def multi_octave_phase(seed: int):
+    """Seeded spectral phase coefficients (GDD in fs^2, TOD in fs^3), uniform in
+    [-MO_GDD_FS2, MO_GDD_FS2] x [-MO_TOD_FS3, MO_TOD_FS3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-MO_GDD_FS2, MO_GDD_FS2), rng.uniform(-MO_TOD_FS3, MO_TOD_FS3)
+
+
+def multi_octave_profile(gdd_fs2: float, tod_fs3: float, L: float, dzeta: float = 2e-7,
+                         lam_min: float = MO_LAM_MIN, lam_max: float = MO_LAM_MAX, edge: float = 0.2,
+                         taper: float = 1e-4, n_fft: int = 1 << 16):
+    """Longitudinal waveform of the multi-octave pulse as samples of a complex
+    (analytic) profile a(zeta), zeta = R - R0, for the tabulated pulse kind.
+
+    Spectrum: amplitude flat in angular frequency over [2 pi c/lam_max, 2 pi c/lam_min]
+    with sin^2 ramps over `edge` of the band at both ends; spectral phase
+    GDD (w - w0)^2 / 2 + TOD (w - w0)^3 / 6 about the mean frequency w0.
+    a(zeta) = -i sum_w S(w) e^{i phase(w)} e^{i w zeta / c} (one-sided, so the real
+    part is the waveform and the imaginary part its quadrature; the factor -i
+    makes the unchirped pulse sine-like at zeta = 0, as Eq. 7), normalised to
+    max |a| = 1, cut to |zeta| <= L/2 with a cos^2 taper over the outer `taper`.
+    Returns (a, zeta0, dzeta, lambda0) with lambda0 = 2 pi c / w0.
+    """
+    c = C_CGS
+    w_lo, w_hi = 2 * math.pi * c / lam_max, 2 * math.pi * c / lam_min
+    w0 = 0.5 * (w_lo + w_hi)
+    dw = 2 * math.pi * c / (n_fft * dzeta)
+    w = dw * np.arange(n_fft)
+    e = edge * (w_hi - w_lo)
+    S = np.zeros(n_fft)
+    S[(w >= w_lo + e) & (w <= w_hi - e)] = 1.0
+    m = (w >= w_lo) & (w < w_lo + e)
+    S[m] = np.sin(0.5 * math.pi * (w[m] - w_lo) / e) ** 2
+    m = (w > w_hi - e) & (w <= w_hi)
+    S[m] = np.sin(0.5 * math.pi * (w_hi - w[m]) / e) ** 2
+    psi = 0.5 * gdd_fs2 * 1e-30 * (w - w0) ** 2 + tod_fs3 * 1e-45 / 6.0 * (w - w0) ** 3
+    # zeta_j = (j - n/2) dzeta: e^{i w_k zeta_j / c} = e^{2 pi i j k / n} (-1)^k
+    a = -1j * n_fft * np.fft.ifft(S * np.exp(1j * psi) * (-1.0) ** np.arange(n_fft))
+    a /= np.abs(a).max()
+    zeta = (np.arange(n_fft) - n_fft // 2) * dzeta
+    sel = np.abs(zeta) <= L / 2
+    a, zeta = a[sel], zeta[sel]
+    edge_dist = L / 2 - np.abs(zeta)
+    tap = np.where(edge_dist < taper, np.sin(0.5 * math.pi * np.clip(edge_dist, 0.0, None) / taper) ** 2, 1.0)
+    return a * tap, float(zeta[0]), dzeta, 2 * math.pi * c / w0
+
+
+def multi_octave_workload(N: int = 1024, seed: int = 0):
+    """Returns (grid, mapping, pulse, profile, n_steps, plane) for the f = 0.5
+    multi-octave focus; profile = (a, zeta0, dzeta).
+
+    Pulse: tabulated kind (flat-top transverse shape, theta = 45 deg, eps = 0.1),
+    waveform of multi_octave_profile with the seed's GDD / TOD, L = 12 um,
+    R0 = 32 um (10 lambda_max).  Layer: D = 50 um along x (D_min = 15.3 um),
+    y, z in [-H, H) with H = R_max sin(theta + eps/2) + 1 um; N cells per axis.
+    dt = (R0/c) / n_steps with n_steps = ceil((R0/c) / Courant value), so the last
+    step lands on the focus.  Focal plane x = 0, 128 x 128 over +-1.5 lambda0.
+    """
+    R0 = 32e-4
+    L = 12e-4
+    D = 50e-4
+    theta = math.atan(1.0 / (2.0 * 0.5))
+    eps = 0.1
+    H = (R0 + L / 2) * math.sin(theta + eps / 2) + 1e-4
+    g = GridSpec(N, N, N, D / N, 2 * H / N, 2 * H / N, -(R0 - L / 2) - D, -H, -H, C_CGS)
+    gdd, tod = multi_octave_phase(seed)
+    a, z0, dz, lam0 = multi_octave_profile(gdd, tod, L)
+    p = PulseSpec(kind=PROFILE, lam=lam0, theta=theta, eps=eps, P0=1e7, n_cycles=1.0, cep=0.0,
+                  ellipticity=0.0, pol_angle=0.0, div_project=1)
+    T = R0 / C_CGS
+    n_steps = int(math.ceil(T / g.courant_dt()))
+    plane = dict(x_p=0.0, ny=128, nz=128, y0=-1.5 * lam0, y1=1.5 * lam0, z0=-1.5 * lam0, z1=1.5 * lam0)
+    return g, MappingSpec(R0, L), p, (a, z0, dz), n_steps, plane

@@ -247,6 +247,44 @@ def test_pulse_fields_transverse_equal_and_converging(kind, ell):
     assert np.all(inward >= -1e-12 * scale ** 2) and np.max(inward) > 0
 
 
+def _eq7_table(lam, L, dz):
+    """Samples of Eq. 7's analytic waveform a = -i e^{i k zeta} cos^2(pi zeta / L)
+    on |zeta| <= L/2 (its real part with a carrier phase phi is sin(k zeta + phi) cos^2)."""
+    z = np.arange(-L / 2, L / 2 + dz / 2, dz)
+    return -1j * np.exp(2j * np.pi * z / lam) * np.cos(np.pi * z / L) ** 2, float(z[0])
+
+
+@pytest.mark.parametrize("cep,ell", [(0.0, 0.0), (1.1, 0.0), (0.4, 0.6)])
+def test_profile_pulse_reproduces_flat_top_from_tabulated_eq7(cep, ell):
+    # R21: the tabulated kind with Eq. 7's waveform as its table is the flat-top
+    # pulse of Eq. 8, up to the linear-interpolation error (k dz)^2 / 8 ~ 1e-6
+    m = O.Mapping(R0=16.0, L=2.0)
+    dz = 1.0 / 2000
+    a, z0 = _eq7_table(1.0, m.L, dz)
+    flat = O.Pulse(kind=O.FLAT_TOP, lam=1.0, theta=0.5, eps=0.1, P0=1.0, cep=cep, ellipticity=ell, pol_angle=0.3)
+    prof = O.Pulse(kind=O.PROFILE, lam=1.0, theta=0.5, eps=0.1, P0=1.0, cep=cep, ellipticity=ell, pol_angle=0.3,
+                   profile=a, profile_z0=z0, profile_dz=dz)
+    Xf, Yf, Zf, Ef, Bf = _pulse_points(flat, m)
+    Xp, Yp, Zp, Ep, Bp = _pulse_points(prof, m)
+    assert np.array_equal(Xf, Xp)
+    scale = np.max(np.abs(Ef))
+    assert scale > 0
+    assert np.max(np.abs(Ep - Ef)) < 5e-6 * scale
+    assert np.max(np.abs(Bp - Bf)) < 5e-6 * scale
+
+
+def test_profile_pulse_is_zero_outside_its_table_and_the_shell():
+    m = O.Mapping(R0=16.0, L=2.0)
+    a = np.ones(11, dtype=np.complex128)
+    p = O.Pulse(kind=O.PROFILE, lam=1.0, theta=0.5, eps=0.1, P0=1.0, profile=a, profile_z0=-0.5, profile_dz=0.1)
+    zeta = np.array([-0.9, -0.51, -0.5, 0.0, 0.5, 0.51, 0.99, 1.2])
+    R = m.R0 + zeta
+    u = O.pulse_scalar(-R, 0 * R, 0 * R, p, m, 1.0, 0.0)
+    A = O.flat_top_A(1.0, 1.0, 0.5)
+    want = np.where(np.abs(zeta) <= 0.5, A / R, 0.0)
+    assert np.allclose(u, want, rtol=1e-15, atol=0)
+
+
 def _cycle_averaged_power(pulse, mapping, c, n_alpha=4000, n_s=64):
     """c/(8 pi) * R0^2 * integral of 2<u^2> over the sphere R = R0 (one carrier period)."""
     amax = min(math.pi, 3.0 * pulse.theta)
