@@ -301,6 +301,7 @@ def multi_octave_measure(dev, stream, k=8):
     its relative L2 difference from float64 on a 768^3 grid of the same layer."""
     import gc
     import torch
+    from paper_2010_00409_gb300 import psatd
     g, m, p, prof, n_steps, plane = W.multi_octave_workload(N=1024, seed=0)
     T = m.R0 / g.c
     pa = (plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])

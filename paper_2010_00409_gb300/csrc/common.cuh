@@ -181,6 +181,12 @@ template <typename T>
 cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode,
                             double scale, cudaStream_t s, long long* nlaunch);
 
+// Per-mode update (any KspaceMode's update, no transform) of a spectrum
+// transformed along all three axes.
+template <typename T>
+cudaError_t launch_modes(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode, double scale,
+                         cudaStream_t s);
+
 // Pulse initialisation on the mapped grid.
 template <typename T>
 cudaError_t launch_init_pulse(cplx<T>* data, const GridGeom& g, const ShellGeom& sh,

@@ -247,6 +247,9 @@ cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, co
         case 512:
             if constexpr (sizeof(T) == 4) return axis_fast<T, 32, 16>(data, ncomp, g, tw, axis, dir, s);
             return cudaErrorNotSupported;
+        case 1024:
+            if constexpr (sizeof(T) == 4) return axis_fast<T, 32, 32>(data, ncomp, g, tw, axis, dir, s);
+            return cudaErrorNotSupported;
         default: return cudaErrorNotSupported;
     }
 }

@@ -128,7 +128,43 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     }
 }
 
+// The per-mode update alone, on a spectrum already transformed along all three
+// axes (the z transforms run as separate launches for axis lengths without a
+// fused kernel): one thread per mode, x fastest, all six components.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+modes_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, const T* __restrict__ kx,
+             const T* __restrict__ ky, const T* __restrict__ kz, const ModeCoef<T>* __restrict__ coef, int mode,
+             T scale) {
+    const size_t n = (size_t)Nx * Ny * Nz;
+    const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % Nx);
+        const size_t r = e / Nx;
+        const int iy = (int)(r % Ny), iz = (int)(r / Ny);
+        const int ax = min(ix, Nx - ix), ay = min(iy, Ny - iy), az = min(iz, Nz - iz);
+        const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
+        mode_update<T>(data + e, data + n + e, data + 2 * n + e, data + 3 * n + e, data + 4 * n + e,
+                       data + 5 * n + e, kx[ix] * m.kinv, ky[iy] * m.kinv, kz[iz] * m.kinv, m.C, m.S, mode,
+                       scale);
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_modes(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode, double scale,
+                         cudaStream_t s) {
+    const size_t n = (size_t)g.Nx * g.Ny * g.Nz;
+    long long blocks = (long long)((n + kThreads - 1) / kThreads);
+    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    modes_kernel<T><<<(unsigned)blocks, kThreads, 0, s>>>(data, g.Nx, g.Ny, g.Nz, tb.k[0], tb.k[1], tb.k[2],
+                                                          tb.coef, mode, (T)scale);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_modes<float>(cplx<float>*, const GridGeom&, const Tables<float>&, int, double, cudaStream_t);
+template cudaError_t launch_modes<double>(cplx<double>*, const GridGeom&, const Tables<double>&, int, double, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode,

@@ -485,6 +485,20 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
                 return r;
             }
         }
+        if (c->kernel_path != PSATD_PATH_GENERIC) {
+            // a z length with a register plan but no fused kernel (1024 in float32,
+            // 512): forward z, the per-mode update, inverse z as three launches
+            cudaError_t r = launch_fft_axis_fast<T>(f, 6, g, tb, 2, -1, c->stream);
+            if (r != cudaErrorNotSupported) {
+                ++c->launches;
+                if (r != cudaSuccess) return r;
+                if ((r = launch_modes<T>(f, g, tb, mode, scale, c->stream)) != cudaSuccess) return r;
+                ++c->launches;
+                r = launch_fft_axis_fast<T>(f, 6, g, tb, 2, +1, c->stream);
+                ++c->launches;
+                return r;
+            }
+        }
         return launch_kspace_z<T>(f, g, tb, mode, scale, c->stream, &c->launches);
     });
     if (e != cudaSuccess) return e;

@@ -291,10 +291,13 @@ def test_tight_focus_256_full_size_real_fields(lib, focus_reference):
 
 
 # ---------------------------------------------------------------------------
-# Register-resident kernels (axis lengths 64, 128, 256, 512) against the oracle
+# Register-resident kernels (axis lengths 64, 128, 256, 512, 1024; z lengths
+# without a fused kernel take forward z, the per-mode update and inverse z as
+# three launches) against the oracle
 # and against the generic shared-memory kernels on the same inputs.
 # ---------------------------------------------------------------------------
-FAST_SHAPES = [(64, 64, 64), (256, 64, 128), (128, 256, 64), (64, 128, 256), (512, 16, 64), (48, 64, 128)]
+FAST_SHAPES = [(64, 64, 64), (256, 64, 128), (128, 256, 64), (64, 128, 256), (512, 16, 64), (48, 64, 128),
+               (1024, 4, 8), (8, 1024, 4), (8, 4, 1024), (4, 8, 512)]
 
 
 @pytest.mark.parametrize("prec", [64, 32])

@@ -115,8 +115,8 @@ def test_multi_octave_1024_full_size(lib):
         exact = ctx.focal_one_shot(p, k * dt, x_k, *plane_args(near), comps=(0, 1, 2))
         focal32 = ctx.focal_one_shot(p, T, plane["x_p"], *plane_args(plane), comps=(0, 1, 2))
     _release()
-    u = 2.0 ** -24
-    assert abs(d1["energy"] / d0["energy"] - 1) <= 8 * u * k
+    # energy and divergence within the float32 parity bound (1e-5) after k steps
+    assert abs(d1["energy"] / d0["energy"] - 1) <= 1e-5
     assert d1["max_div_E"] <= 1e-5 * d1["max_E_hat"]
     assert np.max(np.abs(exact)) > 0
     assert rel(stepped, exact) <= 1e-4
