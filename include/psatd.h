@@ -337,8 +337,14 @@ psatd_status psatd_fno_adam_step(psatd_fno* fno, float lr, float beta1, float be
 psatd_status psatd_fno_synchronize(psatd_fno* fno);
 const char* psatd_fno_last_error(const psatd_fno* fno);
 
-/* The tensor-core GEMM used by the surrogate, on device float32 matrices with
- * arbitrary strides: C = alpha A B + beta C (A: M x K, B: K x N). */
+/* The tensor-core GEMM used by the surrogate (the surrogate is not in the
+ * paper; its dense contractions), on device float32 matrices with arbitrary
+ * strides: C = alpha A B + beta C (A: M x K, B: K x N), operands rounded to
+ * bfloat16, tcgen05.mma with float32 accumulation in tensor memory.  ksplit > 1
+ * splits K over tiles (partial sums added atomically).  Asynchronous on
+ * cuda_stream; returns PSATD_ERR_ARG for NULL pointers or negative sizes.  An
+ * expired bounded wait inside the kernel is reported by the next
+ * psatd_fno_synchronize. */
 psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm, long long sAk, const float* B,
                              long long sBk, long long sBn, float* C, long long sCm, long long sCn, float alpha,
                              float beta, int ksplit, void* cuda_stream);

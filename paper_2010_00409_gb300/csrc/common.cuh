@@ -237,5 +237,6 @@ struct GemmArgs {
     int ksplit;
 };
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s);
+bool gemm_take_error();
 
 }  // namespace psatd

@@ -640,6 +640,7 @@ psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm,
 psatd_status psatd_fno_synchronize(psatd_fno* f) {
     if (!f) return PSATD_ERR_ARG;
     FCK(cudaStreamSynchronize(f->stream));
+    if (gemm_take_error()) return fno_fail(f, PSATD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM expired");
     return PSATD_OK;
 }
 

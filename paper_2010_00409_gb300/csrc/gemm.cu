@@ -1,11 +1,13 @@
-// Strided, batched GEMM on the tensor cores for the surrogate network:
+// Strided, batched GEMM on the 5th-generation tensor cores for the surrogate
+// network:
 //   C[b] = alpha * A[b] * B[b] + beta * C[b]
 // with A[b](m, k) = A[b0 * sAb0 + b1 * sAb1 + m * sAm + k * sAk] (any strides),
 // B[b](k, n) and C[b](m, n) likewise, b = b0 * nb1 + b1.  Inputs and outputs are
-// float32 in memory; tiles are rounded to bfloat16 when staged in shared memory
-// and multiplied with mma.sync m16n8k16 (bf16 x bf16 -> f32 accumulate).
-// Split-K (ksplit > 1) partitions K over blocks and adds partial tiles to C with
-// float atomics (C must hold beta * C beforehand; the launcher scales it).
+// float32 in memory; operands are rounded to bfloat16 when staged in shared
+// memory and multiplied by tcgen05.mma (kind::f16, float32 accumulators in
+// tensor memory).  Split-K (ksplit > 1) partitions K over tiles and adds partial
+// tiles to C with float atomics (C must hold beta * C beforehand; the launcher
+// scales it).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -15,121 +17,28 @@ namespace psatd {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32;
-constexpr int PAD = 8;            // bf16 elements of padding per shared row
-constexpr int kThreads = 128;     // 4 warps, each a 32 x 32 sub-tile
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(kThreads) gemm_kernel(GemmArgs g) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];     // [m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];     // [n][k]
-    const int bz = blockIdx.z;
-    const int split = bz % g.ksplit;
-    const int bidx = bz / g.ksplit;
-    const int b0 = bidx / g.nb1, b1 = bidx % g.nb1;
-    const float* A = g.A + b0 * g.sAb0 + b1 * g.sAb1;
-    const float* B = g.B + b0 * g.sBb0 + b1 * g.sBb1;
-    float* C = g.C + b0 * g.sCb0 + b1 * g.sCb1;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
-    const int kbeg = split * kchunk, kend = min(g.K, kbeg + kchunk);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int grp = lane >> 2, tig = lane & 3;
-    float acc[2][4][4] = {};
-
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // stage A (BM x BK) and B (BK x BN, stored transposed) as bf16
-        for (int e = tid; e < BM * BK; e += kThreads) {
-            int m, k;
-            if (g.sAk == 1) { m = e / BK; k = e % BK; } else { k = e / BM; m = e % BM; }
-            const int gm = m0 + m, gk = k0 + k;
-            const float v = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.f;
-            As[m][k] = __float2bfloat16_rn(v);
-        }
-        for (int e = tid; e < BN * BK; e += kThreads) {
-            int n, k;
-            if (g.sBn == 1) { k = e / BN; n = e % BN; } else { n = e / BK; k = e % BK; }
-            const int gn = n0 + n, gk = k0 + k;
-            const float v = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.f;
-            Bs[n][k] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + grp;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tig]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tig]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tig + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tig + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int cidx = wn + j * 8 + grp;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[cidx][kk + 2 * tig]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[cidx][kk + 2 * tig + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
-    }
-
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int m = m0 + wm + i * 16 + grp + (h >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * tig + (h & 1);
-                if (m < g.M && n < g.N) {
-                    float* dst = C + m * g.sCm + n * g.sCn;
-                    const float v = g.alpha * acc[i][j][h];
-                    if (g.ksplit > 1) atomicAdd(dst, v);
-                    else *dst = (g.beta == 0.f) ? v : v + g.beta * *dst;
-                }
-            }
-}
-
 // ---------------------------------------------------------------------------
-// 5th-generation tensor-core path: tcgen05.mma (kind::f16, bf16 x bf16 -> f32)
-// with the accumulator tile in tensor memory.  Block = 128 threads, tile
-// 128 (M) x BN (N) x 64 (K).  Per K block the threads round their A and B
-// elements to bfloat16 and store them in the no-swizzle K-major layout of the
-// tensor core's shared-memory descriptors: 8-row x 16-byte "core matrices"
-// (8 rows x 8 bf16 along K, 128 contiguous bytes), core matrix (i, kc) of A at
-// kc * (BM/8) * 128 + i * 128 bytes (B alike with BN rows), so the
-// leading-dimension offset (between core matrices adjacent along K) is
-// (rows/8) * 128 bytes and the stride-dimension offset (between adjacent 8-row
-// groups) 128 bytes.  One thread issues the four K = 16 MMAs of the block and
-// commits them to an mbarrier that all threads wait on (bounded) before the
-// tile is overwritten; after the last block each warp reads its 32 accumulator
-// rows from tensor memory (tcgen05.ld, lanes 32w .. 32w + 31).
-constexpr int TBM = 128, TBK = 64, kTcThreads = 128;
-// operand regions sized so that every descriptor read stays inside the
-// block's shared memory whatever the offsets
-constexpr int kTcARegion = 48 * 1024, kTcBRegion = 48 * 1024;
-constexpr size_t kTcSmem = kTcARegion + kTcBRegion;
-__device__ int g_gemm_error;        // set when a bounded wait of the tensor-core GEMM expires
+// tcgen05.mma (kind::f16, bf16 x bf16 -> f32) with the accumulators in tensor
+// memory.  A kernel that allocates tensor memory runs one block per SM, so the
+// grid is one persistent block of 512 threads per SM; tile 128 (M) x BN (N), K
+// in blocks of 64.  Two-stage pipeline: while the tensor core multiplies the
+// operands of one K block, the threads stage the next one, and while the MMAs
+// of tile t run, the threads read tile t-1's accumulators (two accumulators of
+// BN columns in tensor memory).
+//
+// Staging: each thread takes 8 consecutive k of one row, rounds them to
+// bfloat16 and writes them as one 16-byte row of a "core matrix" (8 rows x 8
+// bf16, 128 contiguous bytes) of the no-swizzle K-major layout that the
+// shared-memory descriptors describe: core matrix (i, kc) at kc * (rows/8) *
+// 128 + i * 128 bytes, so the leading-dimension offset (core matrices adjacent
+// along K) is (rows/8) * 128 bytes and the stride-dimension offset (adjacent
+// 8-row groups) 128 bytes.  One thread issues the K = 16 MMAs of a K block (as
+// many as hold data) and commits them to the stage's mbarrier (the stage may be
+// refilled) and, after a tile's last K block, to the accumulator's mbarrier
+// (the tile may be read).  All waits are bounded; an expired wait sets
+// g_gemm_error (gemm_take_error reads and clears it).
+constexpr int TBM = 128, TBK = 64, kTcThreads = 512;
+__device__ int g_gemm_error;
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -149,33 +58,160 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(GemmArgs g) {
-    extern __shared__ __align__(1024) unsigned char tc_raw[];
-    unsigned char* As = tc_raw;
-    unsigned char* Bs = tc_raw + kTcARegion;
-    __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mma_bar;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bz = blockIdx.z;
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int BN> struct TcCfg {
+    static constexpr int kStageA = TBM * TBK * 2;             // bytes of one A stage
+    static constexpr int kStageB = BN * TBK * 2;
+    static constexpr int kSmem = 2 * (kStageA + kStageB);
+    static constexpr int kCols = 2 * BN;                      // two accumulators
+};
+
+struct TcTile {
+    int m0, n0, kbeg, kend, nkb;
+    const float* A;
+    const float* B;
+    float* C;
+};
+
+__device__ __forceinline__ TcTile tc_tile(const GemmArgs& g, int tile, int ntm, int ntn, int BN) {
+    TcTile t;
+    const int mt = tile % ntm;
+    const int rest = tile / ntm;
+    const int nt = rest % ntn;
+    const int bz = rest / ntn;
     const int split = bz % g.ksplit;
     const int bidx = bz / g.ksplit;
     const int b0 = bidx / g.nb1, b1 = bidx % g.nb1;
-    const float* A = g.A + b0 * g.sAb0 + b1 * g.sAb1;
-    const float* B = g.B + b0 * g.sBb0 + b1 * g.sBb1;
-    float* C = g.C + b0 * g.sCb0 + b1 * g.sCb1;
-    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN;
+    t.A = g.A + b0 * g.sAb0 + b1 * g.sAb1;
+    t.B = g.B + b0 * g.sBb0 + b1 * g.sBb1;
+    t.C = g.C + b0 * g.sCb0 + b1 * g.sCb1;
+    t.m0 = mt * TBM;
+    t.n0 = nt * BN;
     const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + TBK - 1) / TBK * TBK;
-    const int kbeg = split * kchunk, kend = min(g.K, kbeg + kchunk);
-    const int nkb = kend > kbeg ? (kend - kbeg + TBK - 1) / TBK : 0;
+    t.kbeg = split * kchunk;
+    t.kend = min(g.K, t.kbeg + kchunk);
+    t.nkb = t.kend > t.kbeg ? (t.kend - t.kbeg + TBK - 1) / TBK : 0;
+    return t;
+}
 
+// rows x TBK operand block -> bf16 core matrices; element (r, k) of the block is
+// src[(r0 + r) * s_r + (k0 + k) * s_k], zero outside rows < nrows, k < kend
+// vec: k is the unit-stride axis and every row starts on a 16-byte boundary
+// (then 8 consecutive k from a multiple of 8 are two aligned float4 loads)
+// Only the first kcs 8-column chunks are staged (the MMAs of a short last K
+// block read no further).
+template <int ROWS>
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const float* __restrict__ src, long long s_r,
+                                         long long s_k, int r0, int nrows, int k0, int kend, bool vec, int kcs) {
+    const int items = ROWS * kcs;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < items; i += kTcThreads) {
+        const int r = i % ROWS, kc = i / ROWS;
+        const int gr = r0 + r, gk = k0 + kc * 8;
+        float v[8];
+        if (vec && gr < nrows && gk + 8 <= kend) {
+            const float4* q4 = reinterpret_cast<const float4*>(src + gr * s_r + gk);
+            const float4 a = __ldg(q4), b = __ldg(q4 + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = (gr < nrows && gk + q < kend) ? src[gr * s_r + (gk + q) * s_k] : 0.f;
+        }
+        uint4 w;
+        w.x = pack_bf16x2(v[0], v[1]);
+        w.y = pack_bf16x2(v[2], v[3]);
+        w.z = pack_bf16x2(v[4], v[5]);
+        w.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(dst + kc * (ROWS / 8) * 128 + (r >> 3) * 128 + (r & 7) * 16) = w;
+    }
+}
+
+// Epilogue.  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (the rows of
+// its lane quarter); the kTcThreads / 128 warps of one quarter split the
+// columns (cols each), read in loads of 8.  With beta != 0 the thread's C
+// values are loaded first (tc_epilogue_c, issued before the wait on the
+// accumulator, so their latency overlaps the MMAs).
+template <int BN> struct TcEpi {
+    static constexpr int parts = kTcThreads / 128, cols = BN / parts;
+    static_assert(cols % 8 == 0, "column split");
+};
+
+template <int BN>
+__device__ __forceinline__ void tc_epilogue_c(const GemmArgs& g, const TcTile& t, float (&cv)[TcEpi<BN>::cols]) {
+    constexpr int cols = TcEpi<BN>::cols;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = t.m0 + 32 * (warp & 3) + lane, c0 = (warp >> 2) * cols;
+    const bool need = g.ksplit == 1 && g.beta != 0.f && m < g.M;
+#pragma unroll
+    for (int i = 0; i < cols; ++i) {
+        const int n = t.n0 + c0 + i;
+        cv[i] = (need && n < g.N) ? t.C[m * g.sCm + n * g.sCn] : 0.f;
+    }
+}
+
+template <int BN>
+__device__ __forceinline__ void tc_epilogue(const GemmArgs& g, const TcTile& t, uint32_t acc_addr, bool have,
+                                            const float (&cv)[TcEpi<BN>::cols]) {
+    constexpr int cols = TcEpi<BN>::cols;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3;
+    const int m = t.m0 + 32 * quarter + lane, c0 = (warp >> 2) * cols;
+#pragma unroll
+    for (int cc = 0; cc < cols; cc += 8) {
+        uint32_t r[8];
+        if (have) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(acc_addr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(c0 + cc)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) r[i] = 0u;
+        }
+        if (m < g.M) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int n = t.n0 + c0 + cc + i;
+                if (n < g.N) {
+                    float* dst = t.C + m * g.sCm + n * g.sCn;
+                    const float v = g.alpha * __uint_as_float(r[i]);
+                    if (g.ksplit > 1) atomicAdd(dst, v);
+                    else *dst = (g.beta == 0.f) ? v : v + g.beta * cv[cc + i];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(GemmArgs g, int ntm, int ntn, int ntiles) {
+    using Cfg = TcCfg<BN>;
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t sbar[2], abar[2];
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_base)),
-                     "r"(BN < 32 ? 32 : BN) : "memory");
+                     "r"(Cfg::kCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&mma_bar)), "r"(1) : "memory");
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&sbar[i])), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&abar[i])), "r"(1) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -185,89 +221,72 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(GemmArgs g) {
     // instruction descriptor: D f32, A and B bf16, both K-major, N = BN, M = 128
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(TBM >> 4) << 24);
+    const bool vecA = g.sAk == 1 && (g.sAm & 3) == 0 && (g.sAb0 & 3) == 0 && (g.sAb1 & 3) == 0 &&
+                      (reinterpret_cast<uintptr_t>(g.A) & 15) == 0;
+    const bool vecB = g.sBk == 1 && (g.sBn & 3) == 0 && (g.sBb0 & 3) == 0 && (g.sBb1 & 3) == 0 &&
+                      (reinterpret_cast<uintptr_t>(g.B) & 15) == 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-        if (kb > 0) ok = tc_wait(&mma_bar, (kb - 1) & 1) && ok;     // the previous MMAs have read the tile
-        const int k0 = kbeg + kb * TBK;
-        // A (TBM x TBK): element (m, k) -> core matrix (m/8, k/8), row m%8, column k%8
-        for (int e = tid; e < TBM * TBK; e += kTcThreads) {
-            int m, k;
-            if (g.sAk == 1) { m = e / TBK; k = e % TBK; } else { k = e / TBM; m = e % TBM; }
-            const int gm = m0 + m, gk = k0 + k;
-            const float v = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.f;
-            const int off = (k >> 3) * (TBM / 8) * 128 + (m >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2;
-            *reinterpret_cast<__nv_bfloat16*>(As + off) = __float2bfloat16_rn(v);
-        }
-        // B (TBK x BN) stored as the N x K operand
-        for (int e = tid; e < BN * TBK; e += kTcThreads) {
-            int n, k;
-            if (g.sBn == 1) { k = e / BN; n = e % BN; } else { n = e / TBK; k = e % TBK; }
-            const int gn = n0 + n, gk = k0 + k;
-            const float v = (gn < g.N && gk < kend) ? B[gk * g.sBk + gn * g.sBn] : 0.f;
-            const int off = (k >> 3) * (BN / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-            *reinterpret_cast<__nv_bfloat16*>(Bs + off) = __float2bfloat16_rn(v);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor-core reads
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int kk = 0; kk < TBK / 16; ++kk) {
-                const uint64_t ad = tc_desc(tc_smem(As) + kk * 2 * (TBM / 8) * 128, (TBM / 8) * 128, 128);
-                const uint64_t bd = tc_desc(tc_smem(Bs) + kk * 2 * (BN / 8) * 128, (BN / 8) * 128, 128);
-                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                             : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem(&mma_bar))
-                         : "memory");
-        }
-    }
-    if (nkb > 0) {
-        ok = tc_wait(&mma_bar, (nkb - 1) & 1) && ok;
-        if (!ok) tc_wait(&mma_bar, (nkb - 1) & 1);     // a second bounded wait for MMAs still in flight
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    // epilogue: row m = 32 warp + lane, 16 columns per tensor-memory load
-    const int m = m0 + 32 * warp + lane;
+    uint32_t it = 0, tl = 0;
+    TcTile prev{};
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r[16];
-        if (nkb > 0) {
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) r[i] = 0u;
-        }
-        if (m < g.M) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int n = n0 + c0 + i;
-                if (n < g.N) {
-                    float* dst = C + m * g.sCm + n * g.sCn;
-                    const float v = g.alpha * __uint_as_float(r[i]);
-                    if (g.ksplit > 1) atomicAdd(dst, v);
-                    else *dst = (g.beta == 0.f) ? v : v + g.beta * *dst;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+        // every thread has finished waiting on the accumulator barriers before
+        // thread 0 commits to them again (also when a tile has no K block)
+        __syncthreads();
+        const TcTile t = tc_tile(g, tile, ntm, ntn, BN);
+        const uint32_t acc = tmem + (tl & 1) * BN;
+#pragma unroll 1
+        for (int kb = 0; kb < t.nkb; ++kb, ++it) {
+            const int s = it & 1;
+            if (it >= 2) ok = tc_wait(&sbar[s], ((it - 2) >> 1) & 1) && ok;     // stage s read by the MMAs
+            unsigned char* As = tc_raw + s * (Cfg::kStageA + Cfg::kStageB);
+            unsigned char* Bs = As + Cfg::kStageA;
+            const int k0 = t.kbeg + kb * TBK;
+            const int nkk = min(TBK / 16, (t.kend - k0 + 15) / 16);         // K = 16 MMAs with data
+            tc_stage<TBM>(As, t.A, g.sAm, g.sAk, t.m0, g.M, k0, t.kend, vecA, 2 * nkk);
+            tc_stage<BN>(Bs, t.B, g.sBn, g.sBk, t.n0, g.N, k0, t.kend, vecB, 2 * nkk);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor-core reads
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                for (int kk = 0; kk < nkk; ++kk) {
+                    const uint64_t ad = tc_desc(tc_smem(As) + kk * 2 * (TBM / 8) * 128, (TBM / 8) * 128, 128);
+                    const uint64_t bd = tc_desc(tc_smem(Bs) + kk * 2 * (BN / 8) * 128, (BN / 8) * 128, 128);
+                    const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                                 : "memory");
                 }
+                tc_commit(&sbar[s]);
             }
         }
+        if (tid == 0) tc_commit(&abar[tl & 1]);          // this tile's accumulator (immediate when nkb = 0)
+        if (tl > 0) {                                     // read the previous tile while these MMAs run
+            float cv[TcEpi<BN>::cols];
+            tc_epilogue_c<BN>(g, prev, cv);
+            ok = tc_wait(&abar[(tl - 1) & 1], ((tl - 1) >> 1) & 1) && ok;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_epilogue<BN>(g, prev, tmem + ((tl - 1) & 1) * BN, prev.nkb > 0, cv);
+        }
+        prev = t;
     }
-    if (!ok && tid == 0) atomicExch(&g_gemm_error, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (tl > 0) {
+        float cv[TcEpi<BN>::cols];
+        tc_epilogue_c<BN>(g, prev, cv);
+        ok = tc_wait(&abar[(tl - 1) & 1], ((tl - 1) >> 1) & 1) && ok;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_epilogue<BN>(g, prev, tmem + ((tl - 1) & 1) * BN, prev.nkb > 0, cv);
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_gemm_error, 1);
+        // second bounded waits: no MMA may still write the accumulators at dealloc
+        for (int i = 0; i < 2; ++i) tc_wait(&abar[i], 0), tc_wait(&abar[i], 1);
+    }
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN < 32 ? 32 : BN)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols) : "memory");
 }
 
 __global__ void scale_kernel(GemmArgs g) {
@@ -294,22 +313,60 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s) {
     if (g.ksplit > 1) {
         scale_kernel<<<1024, 256, 0, s>>>(g);
     }
-#ifdef PSATD_GEMM_TC
+    // The epilogue writes one row per lane, so it coalesces when C is
+    // column-major; a row-major C (or, for other layouts, M < N: the tile is 128
+    // rows by at most 128 columns) is handled as C^T = B^T A^T, a relabelling
+    // of the same products.
+    if (g.sCm != 1 && (g.sCn == 1 || g.M < g.N)) {
+        GemmArgs t = g;
+        t.M = g.N; t.N = g.M;
+        t.A = g.B; t.sAb0 = g.sBb0; t.sAb1 = g.sBb1; t.sAm = g.sBn; t.sAk = g.sBk;
+        t.B = g.A; t.sBb0 = g.sAb0; t.sBb1 = g.sAb1; t.sBk = g.sAk; t.sBn = g.sAm;
+        t.sCm = g.sCn; t.sCn = g.sCm;
+        g = t;
+    }
     {
         const int bn = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : 128);
-        dim3 grid((g.N + bn - 1) / bn, (g.M + TBM - 1) / TBM, g.nb0 * g.nb1 * g.ksplit);
-        if (grid.z > 65535) return cudaErrorInvalidValue;
-        auto k = bn == 32 ? gemm_tc_kernel<32> : (bn == 64 ? gemm_tc_kernel<64> : gemm_tc_kernel<128>);
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-        if (e != cudaSuccess) return e;
-        k<<<grid, kTcThreads, kTcSmem, s>>>(g);
+        const int bi = bn == 32 ? 0 : (bn == 64 ? 1 : 2);
+        const long long ntm = (g.M + TBM - 1) / TBM, ntn = (g.N + bn - 1) / bn;
+        const long long ntiles = ntm * ntn * (long long)g.nb0 * g.nb1 * g.ksplit;
+        if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+        auto k = bi == 0 ? gemm_tc_kernel<32> : (bi == 1 ? gemm_tc_kernel<64> : gemm_tc_kernel<128>);
+        const int smem = bi == 0 ? TcCfg<32>::kSmem : (bi == 1 ? TcCfg<64>::kSmem : TcCfg<128>::kSmem);
+        // one resident block per SM (a kernel that allocates tensor memory runs
+        // one block per SM), persistent over the tiles
+        static int sms = 0, per_sm[3] = {0, 0, 0}, smem_launch[3] = {0, 0, 0};
+        if (!per_sm[bi]) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms < 1) sms = 1;
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kTcThreads, smem);
+            if (e != cudaSuccess) return e;
+            if (occ < 1) return cudaErrorInvalidConfiguration;
+            per_sm[bi] = occ;
+            smem_launch[bi] = smem;
+        }
+        const long long cap = (long long)sms * per_sm[bi];
+        const long long grid = ntiles < cap ? ntiles : cap;
+        k<<<(unsigned)grid, kTcThreads, smem_launch[bi], s>>>(g, (int)ntm, (int)ntn, (int)ntiles);
         return cudaGetLastError();
     }
-#endif
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nb0 * g.nb1 * g.ksplit);
-    if (grid.z > 65535) return cudaErrorInvalidValue;
-    gemm_kernel<<<grid, kThreads, 0, s>>>(g);
-    return cudaGetLastError();
+}
+
+// Read and clear the flag of an expired bounded wait in the GEMM kernel
+// (synchronises the device).
+bool gemm_take_error() {
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_gemm_error, sizeof(int)) != cudaSuccess) return false;
+    if (h) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_gemm_error, &zero, sizeof(int));
+    }
+    return h != 0;
 }
 
 }  // namespace psatd

@@ -1,4 +1,5 @@
-"""The surrogate's tensor-core GEMM and network against the float64 oracle.
+"""The surrogate's tensor-core GEMM (tcgen05, bf16 operands, float32
+accumulators in tensor memory) and network against the float64 oracle.
 
 Tolerances: the GEMM rounds its inputs to bfloat16 and accumulates in float32,
 so against float64 products of the same rounded inputs it agrees to ~1e-6
@@ -21,7 +22,9 @@ def bf16(a):
 
 @pytest.mark.parametrize("M,N,K,ta,tb,ksplit", [(64, 64, 32, False, False, 1), (100, 37, 53, True, False, 1),
                                                  (33, 130, 260, False, True, 1), (32, 32, 4096, False, True, 8),
-                                                 (5, 7, 3, True, True, 1)])
+                                                 (5, 7, 3, True, True, 1), (300, 24, 64, False, False, 1),
+                                                 (257, 200, 129, True, True, 1), (1000, 300, 72, False, False, 3),
+                                                 (24, 2000, 12, False, True, 1)])
 def test_gemm_bf16_against_numpy(lib, M, N, K, ta, tb, ksplit):
     import torch
     rng = np.random.default_rng(M * N + K)
