@@ -57,6 +57,7 @@ def args_parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-multi-octave", action="store_true")
+    ap.add_argument("--no-gemm", action="store_true")
     ap.add_argument("--storage", choices=("real", "complex"), default="real")
     a = ap.parse_args()
     if a.storage == "real" and not real_storage_supported(a.size):
@@ -282,6 +283,8 @@ def run_ours(a):
         line["batched_sweep"] = sweep_measure(dev, stream)
     if not a.no_multi_octave and world == 1:
         line["multi_octave"] = multi_octave_measure(dev, stream)
+    if not a.no_gemm and world == 1:
+        line["surrogate_gemm"] = gemm_measure(dev, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cells, times, sample = oracle_sample_rate(a.size, reps=1)
         line["cpu_baseline"] = {"value": cells / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -334,6 +337,41 @@ def multi_octave_measure(dev, stream, k=8):
             "steps_to_focus": n_steps,
             "one_shot_focal_fields_per_s": 1.0 / t_one,
             "focal_rel_l2_err_vs_fp64_768": float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))}
+
+
+def gemm_measure(dev, stream, n=8192, reps=5):
+    """The surrogate's tensor-core GEMM (tcgen05, bf16 operands rounded from
+    float32, float32 accumulators in tensor memory) on an n^3 problem and on the
+    thin 2^20 x 24 x 64 shape of the surrogate's DFT contractions (column-major C),
+    timed alone with CUDA events; the n^3 rate against the measured bf16 peak."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for name, (M, N, K, col_c) in (("square", (n, n, n, False)), ("thin", (1 << 20, 24, 64, True))):
+            A = torch.randn(M, K, device=dev)
+            B = torch.randn(K, N, device=dev)
+            C = torch.zeros(N, M, device=dev).t() if col_c else torch.zeros(M, N, device=dev)
+            for _ in range(2):
+                psatd.gemm_bf16(A, B, C, stream=stream)
+            e0.record(stream)
+            for _ in range(reps):
+                psatd.gemm_bf16(A, B, C, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            out[name] = {"shape": [M, N, K], "ms": ms, "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}
+            del A, B, C
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = None
+    if os.path.exists(p):
+        with open(p) as fh:
+            peak = json.load(fh).get("bf16_tflops")
+    out["square"]["roofline"] = {"bound": "tensor", "achieved": out["square"]["tflops"], "peak": peak,
+                                 "unit": "TFLOP/s", "frac": out["square"]["tflops"] / peak if peak else None,
+                                 "peak_source": "measured burst bf16 (MEASURED_PEAKS.json bf16_tflops)"}
+    return out
 
 
 def time_jobs(ctx, job, out_dev, steps, stream, dev, profile=False):
