@@ -16,6 +16,13 @@ N > 1 runs one independent replica per GPU (the path does not shard); the
 value is the total work of all ranks over the slowest rank's time.
 --impl reference times the float64 CPU oracle on a bounded sample of the same
 workload (one PSATD step on a 256 x 256 x 64 slab of the grid).
+
+Beside the headline (N = 1 only where noted) the line carries: the other field
+storage, `e2e` (host buffers through the C ABI), `fp64` (the plain float64
+solver), `focal_forms` (one-shot against stepped focal fields), `batched_sweep`
+(64 realisations as one CUDA graph), `multi_octave` (the 1024^3 float32
+multi-octave layer against float64 at 768^3; --multi-octave-steps 0 steps it to
+the focus), `surrogate_gemm` (the tensor-core GEMM) and `cpu_baseline`.
 """
 from __future__ import annotations
 
@@ -58,6 +65,9 @@ def args_parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-multi-octave", action="store_true")
     ap.add_argument("--no-gemm", action="store_true")
+    ap.add_argument("--multi-octave-steps", type=int, default=8,
+                    help="PSATD steps of the 1024^3 multi-octave run (0: to the focus, then the stepped "
+                         "focal field is compared with float64 too)")
     ap.add_argument("--storage", choices=("real", "complex"), default="real")
     a = ap.parse_args()
     if a.storage == "real" and not real_storage_supported(a.size):
@@ -282,7 +292,7 @@ def run_ours(a):
     if not a.no_sweep:
         line["batched_sweep"] = sweep_measure(dev, stream)
     if not a.no_multi_octave and world == 1:
-        line["multi_octave"] = multi_octave_measure(dev, stream)
+        line["multi_octave"] = multi_octave_measure(dev, stream, k=a.multi_octave_steps)
     if not a.no_gemm and world == 1:
         line["surrogate_gemm"] = gemm_measure(dev, stream)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -298,10 +308,11 @@ def run_ours(a):
 
 def multi_octave_measure(dev, stream, k=8):
     """The multi-octave workload (400-3200 nm, seeded GDD / TOD, f = 0.5) on its
-    full 1024^3 float32 layer (complex storage, 51.5 GB; axis length 1024 runs on
-    the generic shared-memory kernels): k PSATD steps timed with CUDA events, the
-    energy drift over them, the focal field at t = R0/c by one exact step, and
-    its relative L2 difference from float64 on a 768^3 grid of the same layer."""
+    full 1024^3 float32 layer (complex storage, 51.5 GB): k PSATD steps timed with
+    CUDA events (k = 0: all steps to the focus t = R0/c), the energy drift over
+    them, the focal field at t = R0/c by one exact step, and its relative L2
+    difference from float64 on a 768^3 grid of the same layer; when the steps
+    reach the focus, the stepped focal field is compared with it too."""
     import gc
     import torch
     from paper_2010_00409_gb300 import psatd
@@ -309,6 +320,10 @@ def multi_octave_measure(dev, stream, k=8):
     T = m.R0 / g.c
     pa = (plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    to_focus = k <= 0
+    if to_focus:
+        k = n_steps
+    stepped = None
     with psatd.Context(g, m, T / n_steps, 32, stream=stream) as ctx:
         ctx.set_pulse_profile(*prof)
         ctx.init_pulse(p)
@@ -318,6 +333,8 @@ def multi_octave_measure(dev, stream, k=8):
         e1.record(stream)
         d1 = ctx.diagnostics()
         ms_step = e0.elapsed_time(e1) / k
+        if to_focus:
+            stepped = ctx.sample_focal_plane(plane["x_p"], *pa, comps=(0, 1, 2))
         ctx.focal_one_shot(p, T, plane["x_p"], *pa, comps=(0, 1, 2))       # warm-up (tables for T)
         t0 = time.perf_counter()
         f32 = ctx.focal_one_shot(p, T, plane["x_p"], *pa, comps=(0, 1, 2))
@@ -330,13 +347,16 @@ def multi_octave_measure(dev, stream, k=8):
         f64 = ctx.focal_one_shot(p2, T, plane2["x_p"], *pa, comps=(0, 1, 2))
     gc.collect()
     torch.cuda.empty_cache()
-    return {"grid": [g.Nx, g.Ny, g.Nz], "precision": "fp32, complex storage", "psatd_steps": k,
+    extra = {}
+    if stepped is not None:
+        extra["stepped_focal_rel_l2_err_vs_fp64_768"] = float(np.linalg.norm(stepped - f64) / np.linalg.norm(f64))
+    return dict({"grid": [g.Nx, g.Ny, g.Nz], "precision": "fp32, complex storage", "psatd_steps": k,
             "ms_per_psatd_step": ms_step, "cell_steps_per_s": g.cells / (ms_step * 1e-3),
             "energy_drift": d1["energy"] / d0["energy"] - 1,
             "max_div_E_rel": d1["max_div_E"] / max(d1["max_E_hat"], 1e-300),
             "steps_to_focus": n_steps,
             "one_shot_focal_fields_per_s": 1.0 / t_one,
-            "focal_rel_l2_err_vs_fp64_768": float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))}
+            "focal_rel_l2_err_vs_fp64_768": float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))}, **extra)
 
 
 def gemm_measure(dev, stream, n=8192, reps=5):

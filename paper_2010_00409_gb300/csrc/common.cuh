@@ -29,6 +29,48 @@ template <typename V> __host__ __device__ __forceinline__ V cmulc(V a, V b) {
     V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
 }
 template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+
+// ---------------------------------------------------------------------------
+// float32 twiddles.  A forward transform multiplies by w and the inverse by
+// conj w, so per step the field's energy is scaled by |w|^2 along every path a
+// twiddle sits on: the rounding of cos and sin to float32 leaves |w|^2 - 1 at
+// ~1e-8 per twiddle, a drift that repeats every step.  Among the float32 pairs
+// within one ulp of (cos, sin) this picks the one minimising
+// |c^2 + s^2 - 1| + |angle error|; values exactly representable stay as they are.
+struct UnitF { float c, s; };
+
+__host__ __device__ constexpr double ulp_f32(double x) {
+    double a = x < 0 ? -x : x, p = 1.0;
+    if (a < 1e-30) return 0.0;
+    if (a >= 1.0) {
+        while (a >= 2.0 * p) p *= 2.0;
+    } else {
+        while (p > a) p *= 0.5;
+    }
+    return p * 1.1920928955078125e-07;            // 2^-23 of the binade
+}
+
+__host__ __device__ constexpr UnitF unit_f32(double c, double s) {
+    const float c0 = (float)c, s0 = (float)s;
+    const bool ce = (double)c0 == c, se = (double)s0 == s;
+    UnitF best{c0, s0};
+    double best_cost = 1e300;
+    for (int i = -1; i <= 1; ++i) {
+        for (int j = -1; j <= 1; ++j) {
+            if ((ce && i != 0) || (se && j != 0)) continue;
+            const float cf = (float)((double)c0 + i * ulp_f32(c0));
+            const float sf = (float)((double)s0 + j * ulp_f32(s0));
+            const double m = (double)cf * cf + (double)sf * sf - 1.0;
+            const double a = c * ((double)sf - s) - s * ((double)cf - c);     // angle error (small)
+            const double cost = (m < 0 ? -m : m) + (a < 0 ? -a : a);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = UnitF{cf, sf};
+            }
+        }
+    }
+    return best;
+}
 // multiply by s*i, s = +-1
 template <typename V> __host__ __device__ __forceinline__ V cmul_si(V a, int s) {
     V r; if (s > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r;

@@ -109,7 +109,18 @@ __host__ __device__ __forceinline__ void reg_pass(const cplx<T> (&in)[N], cplx<T
             if constexpr (Ns > 1 && r > 0 && k > 0) {
                 constexpr double c = ct_cos2pi((long long)r * k, (long long)Ns * R);
                 constexpr double s = (double)S * ct_sin2pi((long long)r * k, (long long)Ns * R);
-                v[r] = cmul(v[r], mk<T>((T)c, (T)s));
+                constexpr bool diag = (c > 0.7 || c < -0.7) && (s > 0.7 || s < -0.7);   // odd multiple of 45 deg
+                if constexpr (sizeof(T) == 4 && diag) {
+                    // (c, s) = (sc, ss) / sqrt 2: exact sign flips, then the compensated 1/sqrt 2
+                    constexpr T sc = c > 0 ? T(1) : T(-1), ss = s > 0 ? T(1) : T(-1);
+                    const cplx<T> u = v[r];
+                    v[r] = mk<T>(mul_rsqrt2<T>(sc * u.x - ss * u.y), mul_rsqrt2<T>(ss * u.x + sc * u.y));
+                } else if constexpr (sizeof(T) == 4) {
+                    constexpr UnitF w = unit_f32(c, s);
+                    v[r] = cmul(v[r], mk<T>(w.c, w.s));
+                } else {
+                    v[r] = cmul(v[r], mk<T>((T)c, (T)s));
+                }
             }
         });
         dft_r<T, R, S>(v);

@@ -60,7 +60,8 @@ constexpr int half_of(int k1) { return (k1 == 0) ? 0 : (k1 == 8 ? 1 : (k1 < 8 ? 
 
 // W_256^k for compile-time k
 template <int K> __device__ __forceinline__ float2 w256() {
-    return make_float2((float)ct_cos2pi(K, 256), (float)-ct_sin2pi(K, 256));
+    constexpr UnitF w = unit_f32(ct_cos2pi(K, 256), -ct_sin2pi(K, 256));
+    return make_float2(w.c, w.s);
 }
 
 // r2c pairing of Z = Z[k] and P = Z[128-k] with w = W_256^k: returns X[k] in *a

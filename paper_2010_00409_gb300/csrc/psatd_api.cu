@@ -211,7 +211,12 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
         std::vector<T> k(N);
         for (int t = 0; t < N; ++t) {
             const double ang = kTwoPi * (double)t / (double)N;
-            tw[t] = mk<T>((T)std::cos(ang), (T)(-std::sin(ang)));
+            if constexpr (sizeof(T) == 4) {
+                const UnitF w = unit_f32(std::cos(ang), -std::sin(ang));
+                tw[t] = mk<T>(w.c, w.s);
+            } else {
+                tw[t] = mk<T>((T)std::cos(ang), (T)(-std::sin(ang)));
+            }
             k[t] = (T)(kTwoPi * (double)freq_index(t, N) / (N * d));
         }
         CK(c, ensure_buf(c->tw[a], N * sizeof(cplx<T>)));
