@@ -22,7 +22,8 @@ storage, `e2e` (host buffers through the C ABI), `fp64` (the plain float64
 solver), `focal_forms` (one-shot against stepped focal fields), `batched_sweep`
 (64 realisations as one CUDA graph), `multi_octave` (the 1024^3 float32
 multi-octave layer against float64 at 768^3; --multi-octave-steps 0 steps it to
-the focus), `surrogate_gemm` (the tensor-core GEMM) and `cpu_baseline`.
+the focus), `surrogate_gemm` (the tensor-core GEMM), `cufft_reference` (cuFFT
+through torch.fft as a library reference) and `cpu_baseline`.
 """
 from __future__ import annotations
 
@@ -65,6 +66,7 @@ def args_parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-multi-octave", action="store_true")
     ap.add_argument("--no-gemm", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--multi-octave-steps", type=int, default=8,
                     help="PSATD steps of the 1024^3 multi-octave run (0: to the focus, then the stepped "
                          "focal field is compared with float64 too)")
@@ -295,6 +297,8 @@ def run_ours(a):
         line["multi_octave"] = multi_octave_measure(dev, stream, k=a.multi_octave_steps)
     if not a.no_gemm and world == 1:
         line["surrogate_gemm"] = gemm_measure(dev, stream)
+    if not a.no_cufft and world == 1 and a.size == 256:
+        line["cufft_reference"] = cufft_measure(dev, stream, g, dt, line)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cells, times, sample = oracle_sample_rate(a.size, reps=1)
         line["cpu_baseline"] = {"value": cells / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -357,6 +361,70 @@ def multi_octave_measure(dev, stream, k=8):
             "steps_to_focus": n_steps,
             "one_shot_focal_fields_per_s": 1.0 / t_one,
             "focal_rel_l2_err_vs_fp64_768": float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))}, **extra)
+
+
+def cufft_measure(dev, stream, g, dt, line, reps=5):
+    """Library reference (not a path of this package): cuFFT through torch.fft on
+    the same six 256^3 fields — forward plus inverse 3D transforms of complex64
+    storage and real-to-complex / complex-to-real transforms of float32 storage —
+    and, for the complex step, the Eq. 3-4 rotation as PyTorch elementwise
+    operations; timed with CUDA events on the bench's stream."""
+    import torch
+    N = g.Nx
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        x = torch.randn(6, N, N, N, device=dev, dtype=torch.complex64)
+        out["complex_fwd_inv_ms"] = timed(lambda: torch.fft.ifftn(torch.fft.fftn(x, dim=(1, 2, 3)), dim=(1, 2, 3)))
+        # per-mode rotation (C = cos(c|k|dt)/1, S = sin(c|k|dt), unit k) on the spectrum
+        kx = (2 * np.pi * np.fft.fftfreq(N, g.dx)).astype(np.float32)
+        ky = (2 * np.pi * np.fft.fftfreq(N, g.dy)).astype(np.float32)
+        kz = (2 * np.pi * np.fft.fftfreq(N, g.dz)).astype(np.float32)
+        KX = torch.tensor(kx, device=dev)[None, None, :]
+        KY = torch.tensor(ky, device=dev)[None, :, None]
+        KZ = torch.tensor(kz, device=dev)[:, None, None]
+        km = torch.sqrt(KX * KX + KY * KY + KZ * KZ)
+        inv = torch.where(km > 0, 1.0 / torch.clamp(km, min=1e-30), torch.zeros_like(km))
+        nx, ny, nz = KX * inv, KY * inv, KZ * inv
+        C = torch.cos(g.c * km * dt).to(torch.complex64)
+        S = (1j * torch.sin(g.c * km * dt)).to(torch.complex64)
+        X = torch.fft.fftn(x, dim=(1, 2, 3))
+
+        def rotate():
+            Ex, Ey, Ez, Bx, By, Bz = X.unbind(0)
+            kE = nx * Ex + ny * Ey + nz * Ez
+            return torch.stack([C * (Ex - nx * kE) + S * (ny * Bz - nz * By),
+                                C * (Ey - ny * kE) + S * (nz * Bx - nx * Bz),
+                                C * (Ez - nz * kE) + S * (nx * By - ny * Bx),
+                                C * Bx - S * (ny * Ez - nz * Ey),
+                                C * By - S * (nz * Ex - nx * Ez),
+                                C * Bz - S * (nx * Ey - ny * Ex)])
+        out["complex_rotation_torch_ms"] = timed(rotate)
+        del X, x
+        xr = torch.randn(6, N, N, N, device=dev, dtype=torch.float32)
+        out["real_fwd_inv_ms"] = timed(lambda: torch.fft.irfftn(torch.fft.rfftn(xr, dim=(1, 2, 3)), s=(N, N, N),
+                                                                dim=(1, 2, 3)))
+        del xr
+    torch.cuda.empty_cache()
+    ours_real = line.get("step_hbm", {}).get("ms_per_psatd_step")
+    ours_cplx = line.get("complex_storage", {}).get("step_hbm", {}).get("ms_per_psatd_step")
+    out["complex_step_ms"] = out["complex_fwd_inv_ms"] + out["complex_rotation_torch_ms"]
+    out["note"] = ("cuFFT forward + inverse alone, before any update, against this package's whole step: "
+                   "real %.3f ms vs %.3f ms, complex %.3f ms vs %.3f ms" %
+                   (out["real_fwd_inv_ms"], ours_real or float("nan"), out["complex_fwd_inv_ms"],
+                    ours_cplx or float("nan")))
+    return out
 
 
 def gemm_measure(dev, stream, n=8192, reps=5):
