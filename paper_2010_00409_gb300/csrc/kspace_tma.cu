@@ -140,6 +140,19 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     cplx<T>* own = spec + j * W + c;                           // (row r, position (c, j)) at own[r * RP]
     cplx<T> v[NB][N1];
 
+    // Exchange layout: between the two passes of a transform, odd rows hold
+    // their column pairs (2m, 2m + 1) swapped, i.e. logical column n of row k
+    // sits at column n ^ (k & 1).  A half-warp (quarter-warp in FP64) spans
+    // lanes j = 2m, 2m + 1; in the exchange it reads (writes) one row per lane,
+    // two rows RP apart on the same banks, and the swap sends its two rows to
+    // columns of opposite parity, i.e. to the two halves of the bank array, so
+    // no access of the exchange has a bank conflict.  Row parity and column
+    // parity are known per access, so every access is a fixed base pointer
+    // plus an immediate offset.
+    static_assert(N2 % 2 == 0, "row parity of the exchange row = parity of j");
+    const int odd = j & 1;
+    cplx<T>* own_x = spec + (j ^ 1) * W + c;                   // position (c, j) of an odd row
+
     // forward z transforms of this group's components, NB per exchange round
 #pragma unroll 1
     for (int q0 = NC * h; q0 < NC * h + NC; q0 += NB) {
@@ -153,7 +166,11 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 constexpr int k1 = decltype(kc)::value;
                 if (j) v[b][k1] = cmul(v[b][k1], twr[k1]);
             });
-            static_for<0, N1>([&](auto kc) { sl[decltype(kc)::value * RP] = v[b][decltype(kc)::value]; });
+            cplx<T>* sx = own_x + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto kc) {
+                constexpr int k1 = decltype(kc)::value;
+                ((k1 & 1) ? sx : sl)[k1 * RP] = v[b][k1];
+            });
         });
         group_sync<NT, G>(h);
         static_for<0, NB>([&](auto bc) {
@@ -163,7 +180,12 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 constexpr int q = decltype(qc)::value;
                 cplx<T> w[N2];
                 const cplx<T>* row = sl + (j + N2 * q) * RP;
-                static_for<0, N2>([&](auto jc) { w[decltype(jc)::value] = row[decltype(jc)::value * W]; });
+                const cplx<T>* ev = row + odd * W;              // even columns of this row's parity
+                const cplx<T>* od = row - odd * W;              // odd columns
+                static_for<0, N2>([&](auto jc) {
+                    constexpr int n = decltype(jc)::value;
+                    w[n] = ((n & 1) ? od : ev)[n * W];
+                });
                 reg_dft<T, -1, N2>(w);
                 static_for<0, N2>([&](auto kc) { v[b][q * N2 + decltype(kc)::value] = w[decltype(kc)::value]; });
             });
@@ -235,6 +257,8 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 reg_dft<T, +1, N2>(w);
                 const int k1 = j + N2 * q;
                 cplx<T>* row = sl + k1 * RP;
+                cplx<T>* ev = row + odd * W;                    // even columns of this row's parity
+                cplx<T>* od = row - odd * W;                    // odd columns
                 static_for<0, N2>([&](auto nc) {
                     constexpr int n2 = decltype(nc)::value;
                     cplx<T> val = w[n2];
@@ -243,7 +267,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                         const cplx<T> tv = (q == 0) ? twr[n2] : tw[n2 * k1];
                         val = cmulc(val, tv);
                     }
-                    row[n2 * W] = val;
+                    ((n2 & 1) ? od : ev)[n2 * W] = val;
                 });
             });
         });
@@ -251,7 +275,11 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             const cplx<T>* sl = own + (q0 + b) * SLOT;
-            static_for<0, N1>([&](auto kc) { v[b][decltype(kc)::value] = sl[decltype(kc)::value * RP]; });
+            const cplx<T>* sx = own_x + (q0 + b) * SLOT;
+            static_for<0, N1>([&](auto kc) {
+                constexpr int k1 = decltype(kc)::value;
+                v[b][k1] = ((k1 & 1) ? sx : sl)[k1 * RP];
+            });
         });
         static_for<0, NB>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
