@@ -19,7 +19,8 @@ workload (one PSATD step on a 256 x 256 x 64 slab of the grid).
 
 Beside the headline (N = 1 only where noted) the line carries: the other field
 storage, `e2e` (host buffers through the C ABI), `fp64` (the plain float64
-solver), `focal_forms` (one-shot against stepped focal fields), `batched_sweep`
+solver, with its arithmetic roofline against the float64 FMA rate measured in
+the same run), `focal_forms` (one-shot against stepped focal fields), `batched_sweep`
 (64 realisations as one CUDA graph), `multi_octave` (the 1024^3 float32
 multi-octave layer against float64 at 768^3; --multi-octave-steps 0 steps it to
 the focus), `surrogate_gemm` (the tensor-core GEMM), `cufft_reference` (cuFFT
@@ -29,6 +30,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -547,10 +549,35 @@ def e2e_measure(a, ctx, g, m, p, n_steps, plane, stream, dev, world):
             "steps": k, "ms_per_step": 1e3 * t / k}
 
 
-def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
-    """The plain float64 GPU solver on the same grid: n PSATD steps."""
+def fp64_peak_measure(dev, stream, iters=4096, reps=5):
+    """Float64 FMA rate of this GPU (TFLOP/s): the library's probe kernel, eight
+    independent FMA chains per thread, 8 blocks of 256 threads per SM, timed with
+    CUDA events on the launching stream after two warm-up launches."""
     import torch
     from paper_2010_00409_gb300 import psatd
+    blocks, threads = 8 * torch.cuda.get_device_properties(dev).multi_processor_count, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        psatd.fp64_fma_probe(out, blocks, threads, iters, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        psatd.fp64_fma_probe(out, blocks, threads, iters, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    assert bool(torch.isfinite(out).all())
+    return 16.0 * iters * blocks * threads / (ms * 1e-3) / 1e12
+
+
+def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
+    """The plain float64 GPU solver on the same grid: n PSATD steps, with its
+    arithmetic roofline: nominal flops per cell-step (5 N log2 N per complex
+    transform of N points, forward and inverse, six components, plus 80 for the
+    per-mode update) against the float64 FMA rate measured by the probe."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    peak = fp64_peak_measure(dev, stream)
     with psatd.Context(g, m, dt, 64, stream=stream) as c:
         c.init_pulse(p)
         c.advance(2)
@@ -564,8 +591,13 @@ def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
         prof = c.profile_read()
+    flop = 2 * 6 * 5 * math.log2(g.cells) + 80
+    achieved = flop * g.cells * n / (ms * 1e-3) / 1e12
     return {"value": g.cells * n / (ms / 1e3), "unit": UNIT, "psatd_steps": n, "ms_per_psatd_step": ms / n,
-            "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()}}
+            "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flop_per_cell_step": flop,
+                         "peak_source": "measured in this run: float64 FMA chains (psatd_fp64_fma_probe)"}}
 
 
 def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_step64, reps=5):

@@ -349,6 +349,18 @@ psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm,
                              long long sBk, long long sBn, float* C, long long sCm, long long sCn, float alpha,
                              float beta, int ksplit, void* cuda_stream);
 
+/* Float64 arithmetic rate probe, the denominator of the float64 solver's
+ * roofline (that path is bound by float64 arithmetic, not by memory): launches
+ * blocks x threads threads on cuda_stream; each runs eight independent chains
+ * of iters float64 fused multiply-adds, i.e. 16 * iters floating-point
+ * operations per thread, and writes one double to out[thread] (device memory
+ * of blocks * threads doubles, owned by the caller).  The caller times the
+ * launch (CUDA events on the same stream).  PSATD_ERR_ARG for a NULL out,
+ * blocks outside 1..2^20, threads not a multiple of 32 in 32..1024 or
+ * iters < 1; PSATD_ERR_CUDA if the launch fails.  Asynchronous.  The paper has
+ * no counterpart. */
+psatd_status psatd_fp64_fma_probe(double* out, int blocks, int threads, int iters, void* cuda_stream);
+
 /* Kernel kinds for per-kernel timing. */
 enum {
     PSATD_KERNEL_FFT_X = 0,      /* generic FFT along x */

@@ -33,7 +33,7 @@ EXPORTS = (
     "psatd_batch_nodes", "psatd_batch_destroy", "psatd_autotune",
     "psatd_fno_create", "psatd_fno_destroy", "psatd_fno_num_params", "psatd_fno_buffers", "psatd_fno_forward",
     "psatd_fno_loss_backward", "psatd_fno_adam_step", "psatd_fno_synchronize", "psatd_fno_last_error",
-    "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile",
+    "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile", "psatd_fp64_fma_probe",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_fno_synchronize": (C.c_int, [P]),
         "psatd_fno_last_error": (C.c_char_p, [P]),
         "psatd_set_mapping": (C.c_int, [P, C.POINTER(PsatdMapping)]),
+        "psatd_fp64_fma_probe": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P]),
         "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
                                       C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }
@@ -298,6 +299,17 @@ def gemm_bf16(A, B, Cout, alpha=1.0, beta=0.0, ksplit=1, stream=None):
                                alpha, beta, ksplit, C.c_void_p(s.cuda_stream))
     _check(st, None)
     return Cout
+
+
+def fp64_fma_probe(out, blocks, threads, iters, stream=None):
+    """Launch the float64 FMA rate probe (16 * iters flops per thread) writing
+    one float64 per thread to the CUDA tensor out (blocks * threads elements)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    assert out.dtype == torch.float64 and out.is_cuda and out.numel() >= blocks * threads
+    _check(lib().psatd_fp64_fma_probe(C.c_void_p(out.data_ptr()), blocks, threads, iters,
+                                      C.c_void_p(s.cuda_stream)), None)
+    return out
 
 
 class Context:

@@ -66,6 +66,12 @@ def test_bad_arguments_rejected_without_device(L):
     assert lib.psatd_advance(None, 1) == L.ERR_ARG
     assert lib.psatd_time(None) == 0.0
     assert lib.psatd_status_string(L.ERR_SIZE) == b"PSATD_ERR_SIZE"
+    buf = C.c_void_p(8)   # never dereferenced: every call below fails its argument check first
+    assert lib.psatd_fp64_fma_probe(None, 1, 32, 1, None) == L.ERR_ARG
+    assert lib.psatd_fp64_fma_probe(buf, 0, 32, 1, None) == L.ERR_ARG
+    assert lib.psatd_fp64_fma_probe(buf, 1, 48, 1, None) == L.ERR_ARG
+    assert lib.psatd_fp64_fma_probe(buf, 1, 2048, 1, None) == L.ERR_ARG
+    assert lib.psatd_fp64_fma_probe(buf, 1, 32, 0, None) == L.ERR_ARG
 
 
 def test_d_min_host_helper_matches_oracle(L):
