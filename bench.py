@@ -24,7 +24,8 @@ the same run), `focal_forms` (one-shot against stepped focal fields), `batched_s
 (64 realisations as one CUDA graph), `multi_octave` (the 1024^3 float32
 multi-octave layer against float64 at 768^3; --multi-octave-steps 0 steps it to
 the focus), `surrogate_gemm` (the tensor-core GEMM), `cufft_reference` (cuFFT
-through torch.fft as a library reference) and `cpu_baseline`.
+through torch.fft as a library reference), `cpu_baseline` (the oracle on one
+host core) and `cpu_baseline_all_cores` (one oracle process per host core).
 """
 from __future__ import annotations
 
@@ -172,6 +173,30 @@ def oracle_sample_rate(size: int, reps: int = 1):
         g.Nx, g.Ny, nz, size)
 
 
+def _oracle_worker(size):
+    """One spawned process: a warm-up step, then one timed oracle step (seconds)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    cells, _, _ = oracle_sample_rate(size, reps=1)
+    _, times, _ = oracle_sample_rate(size, reps=1)
+    return cells, times[0]
+
+
+def oracle_all_cores_rate(size, procs=None, timeout_s=300):
+    """The same oracle sample run as one independent process per host core
+    (started with spawn, so none is forked from a process that holds a CUDA
+    context); rate = all processes' cells / the slowest process's step time."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map_async(_oracle_worker, [size] * procs).get(timeout=timeout_s)
+    cells = sum(c for c, _ in res)
+    t = max(dt for _, dt in res)
+    return {"value": cells / t, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": "%d independent processes, each one float64 oracle PSATD step (1 thread) on a "
+                      "%dx%dx%d slab of the %d^3 grid after one warm-up step; rate = their cells / the "
+                      "slowest step" % (procs, size, size, max(1, size // 4), size)}
+
+
 def run_reference(a):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -305,6 +330,10 @@ def run_ours(a):
         cells, times, sample = oracle_sample_rate(a.size, reps=1)
         line["cpu_baseline"] = {"value": cells / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample}
+        try:
+            line["cpu_baseline_all_cores"] = oracle_all_cores_rate(a.size)
+        except Exception as e:  # reported, never fatal: the GPU figures above stand without it
+            line["cpu_baseline_all_cores"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -23,3 +23,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["grid"] == [32, 32, 32]
+
+
+def test_all_cores_oracle_rate_runs_spawned_processes():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_all_cores_rate(32, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "cell-steps/s" and r["value"] > 0
