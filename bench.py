@@ -186,7 +186,13 @@ def oracle_all_cores_rate(size, procs=None, timeout_s=300):
     (started with spawn, so none is forked from a process that holds a CUDA
     context); rate = all processes' cells / the slowest process's step time."""
     import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
+    if procs is None:
+        # the cores this process may run on, at most 16, and at most a quarter of the
+        # free host memory at ~2.5 GB per process (the 256^3 sample peaks near 2 GB)
+        procs = min(len(os.sched_getaffinity(0)), 16)
+        free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        per = 2.5e9 * (size / 256) ** 3
+        procs = max(1, min(procs, int(0.25 * free / per)))
     with mp.get_context("spawn").Pool(procs) as pool:
         res = pool.map_async(_oracle_worker, [size] * procs).get(timeout=timeout_s)
     cells = sum(c for c, _ in res)
