@@ -60,8 +60,8 @@ __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-// z[b][c][v] += bias[c]; a = act(z) (act = GELU if gelu else identity)
-__global__ void bias_act_kernel(float* __restrict__ z, float* __restrict__ a, const float* __restrict__ bias,
+// z[b][c][v] += bias[c]; a = act(z) (act = GELU if gelu else identity); a may be z
+__global__ void bias_act_kernel(float* z, float* a, const float* __restrict__ bias,
                                 int B, int C, long long nv, int use_gelu) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)B * C * nv;
          e += (long long)gridDim.x * blockDim.x) {
@@ -72,8 +72,8 @@ __global__ void bias_act_kernel(float* __restrict__ z, float* __restrict__ a, co
     }
 }
 
-// g_z = g_a * act'(z)
-__global__ void act_back_kernel(const float* __restrict__ z, const float* __restrict__ ga, float* __restrict__ gz,
+// g_z = g_a * act'(z); g_z may be g_a
+__global__ void act_back_kernel(const float* __restrict__ z, const float* ga, float* gz,
                                 long long n, int use_gelu) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         gz[e] = use_gelu ? ga[e] * gelu_grad(z[e]) : ga[e];
@@ -484,9 +484,8 @@ psatd_status fno_forward(psatd_fno* f, const float* prm, int B) {
     bias_act_kernel<<<grid_for(B * H * NV), 256, 0, s>>>(f->zq, f->hq, f->par + f->o_q1_b, B, H, NV, 1);
     FCK(launch_gemm(G(NO, (int)NV, H, f->par + f->o_q2_w, H, 1, f->hq, NV, 1, f->out, NV, 1, 0.f, B, 0, H * NV,
                       NO * NV), s));
-    float* dummy = f->gout;   // bias only (no activation): out += b
+    // bias only (no activation): out += b, in place
     bias_act_kernel<<<grid_for(B * NO * NV), 256, 0, s>>>(f->out, f->out, f->par + f->o_q2_b, B, NO, NV, 0);
-    (void)dummy;
     FCK(cudaGetLastError());
     return PSATD_OK;
 }

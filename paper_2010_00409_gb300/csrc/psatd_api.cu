@@ -87,7 +87,7 @@ struct psatd_ctx {
     DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
     DevBuf slot_k, slot_coef;           // real fields: k_x per slot, coefficient table in slot order
     DevBuf nyq;                         // real fields: x Nyquist spectrum [6][Nz][Ny] between the plane kernels
-    alignas(64) CUtensorMap nyq_map;    // ... and its tensor map for the k-space kernel
+    CUtensorMap nyq_map;                // ... and its tensor map for the k-space kernel (128-B aligned type)
     bool nyq_map_ok = false;
 
     // tables (device)
@@ -109,7 +109,7 @@ struct psatd_ctx {
     int tile_shift = 0;                 // generic-kernel tile width scale (autotuner)
 
     // tensor map of the field storage for the copy-engine-fed k-space kernel
-    alignas(64) CUtensorMap field_map;
+    CUtensorMap field_map;              // (the type is 128-byte aligned)
     void* field_map_ptr = nullptr;      // storage the map was encoded for
     bool field_map_real = false;        // ... and whether as a real-field half spectrum
     bool field_map_ok = false;
