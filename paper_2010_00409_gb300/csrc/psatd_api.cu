@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <mutex>
@@ -312,10 +313,17 @@ cudaError_t harvest(psatd_ctx* c, size_t upto) {
     return cudaSuccess;
 }
 
-// Run one launch (or a group of launches) of kernel kind `kind`, bracketed by
-// events when profiling is on.
+// Run one launch (or a group of launches) of kernel kind `kind` inside an NVTX
+// range named for the kind (visible to Nsight tools; a no-op without one), and
+// bracketed by events when profiling is on.
+struct NvtxRange {
+    explicit NvtxRange(int kind) { nvtxRangePushA(psatd_kernel_name(kind)); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <typename F>
 cudaError_t timed(psatd_ctx* c, int kind, F&& launch) {
+    NvtxRange range(kind);
     if (!c->prof_on) return launch();
     cudaEvent_t a = take_event(c), b = take_event(c);
     if (!a || !b) return cudaErrorMemoryAllocation;
