@@ -1,0 +1,104 @@
+"""A physical pin of the oracle's whole focusing chain: Gaussian pulse amplitude
+(Sec. 3.2.1), transverse profile, initialisation on the mapped periodic layer
+with its replicas (Sec. 2.3), the exact PSATD propagation (Sec. 2.1) and the
+focal sampling (Eq. 14-16), against the diffraction integral of a converging
+spherical wave and against the paper's paraxial limit.
+
+Debye's integral: a spherical wave converging from the sphere R = R0 with
+carrier amplitude E0 A(alpha) and polarisation s0(alpha, phi) has, at the
+focus and in the short-wavelength limit (k R0 >> 1), the carrier amplitude
+
+    E(0) = (k R0 / 2 pi) * integral of E0 A(alpha) s0 dOmega.
+
+With d = y, s0 = (d - (d.R^) R^) / |...| has y component sqrt(1 - R^_y^2) and
+its x and z components integrate to zero, so
+
+    |E_y(0)| = k R0 E0 int_0^pi A(alpha) <sqrt(1 - sin^2 alpha cos^2 phi)>_phi
+                   sin alpha dalpha.
+
+For the untruncated Gaussian A = exp(-alpha^2/theta0^2) and small theta0 this
+tends to the paraxial focus I0 = 2 P0 / (pi w0^2), w0 = 2 f lambda / pi, that
+the paper uses to validate its solver in the weak-focusing limit (Sec. 3.2.1;
+cycle-averaged CGS intensity c E^2 / (8 pi)).  The oracle's profile also has
+the Eq. 5 edge at 2 theta0, which lowers the focal field by a few per cent.
+"""
+import math
+
+import numpy as np
+
+from oracle import psatd_oracle as O
+
+LAM, R0, C, P0, EPS, N_CYCLES = 1.0, 20.0, 1.0, 1.0, 0.1, 4.0
+
+
+def smooth235(n):
+    while True:
+        k = n
+        for p in (2, 3, 5):
+            while k % p == 0:
+                k //= p
+        if k == 1:
+            return n
+        n += 1
+
+
+def edge_window(alpha, theta, eps):
+    """1 up to theta - eps/2, a cos^2 ramp to 0 at theta + eps/2 (Eq. 5)."""
+    ramp = np.cos(np.pi * (alpha - theta + eps / 2) / (2 * eps)) ** 2
+    return np.where(alpha <= theta - eps / 2, 1.0, np.where(alpha <= theta + eps / 2, ramp, 0.0))
+
+
+def debye_focal_field(theta0, truncated):
+    """|E_y| at the focus from Debye's integral, with E0 from the printed
+    normalisation (power P0 through the sphere) and F by quadrature."""
+    a = np.linspace(0.0, math.pi, 400001)
+    F = np.trapezoid(np.sin(a) * np.exp(-2 * a * a / theta0 ** 2), a)
+    E0 = math.sqrt(4 * P0 / (C * R0 * R0 * F))          # SI E0 of Sec. 3.2.1 with eps0 -> 1/(4 pi)
+    A = np.exp(-a * a / theta0 ** 2)
+    if truncated:
+        A = A * edge_window(a, 2 * theta0, EPS)
+    phi = np.linspace(0.0, 2 * math.pi, 721)[:-1]
+    s_coarse = np.sin(a[::400])
+    pol = np.sqrt(1.0 - np.outer(s_coarse ** 2, np.cos(phi) ** 2)).mean(axis=1)
+    pol = np.interp(a, a[::400], pol)
+    k = 2 * math.pi / LAM
+    return k * R0 * E0 * np.trapezoid(A * pol * np.sin(a), a)
+
+
+def oracle_focal_field(fnum, ppl=6):
+    """Amplitude of E at the focus at t = R0/c from the oracle: init on the
+    mapped layer, one exact step, sampling at the origin; the carrier amplitude
+    from two samples a quarter period apart."""
+    theta0 = O.theta_from_fnumber(fnum)
+    L = 4.5 * N_CYCLES * LAM
+    m = O.Mapping(R0, L)
+    D = O.d_min(R0, L, 2 * theta0 + EPS) + LAM
+    H = m.R_max * math.sin(2 * theta0 + EPS / 2) + LAM
+    d = LAM / ppl
+    Nx, Nt = smooth235(int(math.ceil(D / d))), smooth235(int(math.ceil(2 * H / d)))
+    g = O.Grid(Nx, Nt, Nt, d, d, d, -(R0 - L / 2) - Nx * d, -Nt * d / 2, -Nt * d / 2, C)
+    p = O.Pulse(kind=O.GAUSSIAN, lam=LAM, theta=theta0, eps=EPS, P0=P0, n_cycles=N_CYCLES)
+    f0 = O.init_fields(g, m, p)
+    T = R0 / C
+    samples = []
+    for t in (T, T + LAM / (4 * C)):
+        s = O.sample_plane(O.advance_exact(f0, g, t), g, m, 0.0, np.array([0.0]), np.array([0.0]), t)
+        samples.append(s[:, 0, 0].real)
+    return np.sqrt(samples[0] ** 2 + samples[1] ** 2)
+
+
+def test_gaussian_focus_matches_debye_integral_and_paraxial_limit():
+    fnum = 4.0
+    theta0 = math.atan(1.0 / (2 * fnum))
+    E = oracle_focal_field(fnum)
+    Ed = debye_focal_field(theta0, truncated=True)
+    # the y-polarised pulse focuses to E_y; E_x and E_z vanish on the axis
+    assert E[0] < 1e-6 * E[1] and E[2] < 1e-6 * E[1]
+    assert abs(E[1] / Ed - 1.0) < 1e-3
+    # the untruncated Gaussian reaches the paraxial focus up to O(theta0^2)
+    w0 = 2 * fnum * LAM / math.pi
+    E_par = math.sqrt(16 * P0 / (C * w0 * w0))
+    assert abs(debye_focal_field(theta0, truncated=False) / E_par - 1.0) < 0.02
+    # and the oracle's intensity sits just below I0, by the edge at 2 theta0
+    ratio = (E[1] / E_par) ** 2
+    assert 0.9 < ratio < 1.0
