@@ -16,6 +16,11 @@ its x and z components integrate to zero, so
     |E_y(0)| = k R0 E0 int_0^pi A(alpha) <sqrt(1 - sin^2 alpha cos^2 phi)>_phi
                    sin alpha dalpha.
 
+For a pulse of any duration the time-domain form of the same integral gives
+the field at the focus at t = R0/c from the slope of the longitudinal profile at
+its centre: u_l(s) = sin(k s) cos^2(pi s / L) of Eq. 7 has slope k there, so the
+flat-top pulse of Eq. 8-9 reaches |E_y(0)| = k A int u_ts sqrt(...) sin alpha.
+
 For the untruncated Gaussian A = exp(-alpha^2/theta0^2) and small theta0 this
 tends to the paraxial focus I0 = 2 P0 / (pi w0^2), w0 = 2 f lambda / pi, that
 the paper uses to validate its solver in the weak-focusing limit (Sec. 3.2.1;
@@ -48,6 +53,25 @@ def edge_window(alpha, theta, eps):
     return np.where(alpha <= theta - eps / 2, 1.0, np.where(alpha <= theta + eps / 2, ramp, 0.0))
 
 
+def polarisation_average(a):
+    """<sqrt(1 - sin^2 a cos^2 phi)>_phi: the y component of s0 averaged over phi."""
+    phi = np.linspace(0.0, 2 * math.pi, 721)[:-1]
+    coarse = a[::400]
+    pol = np.sqrt(1.0 - np.outer(np.sin(coarse) ** 2, np.cos(phi) ** 2)).mean(axis=1)
+    return np.interp(a, coarse, pol)
+
+
+def layer_grid(theta_support, R0, L, ppl=6):
+    """Mapped layer for a shell whose profile ends at the angle theta_support:
+    period D = D_min (Eq. 12) + lambda, transverse half width R_max sin + lambda."""
+    m = O.Mapping(R0, L)
+    D = O.d_min(R0, L, theta_support) + LAM
+    H = m.R_max * math.sin(theta_support) + LAM
+    d = LAM / ppl
+    Nx, Nt = smooth235(int(math.ceil(D / d))), smooth235(int(math.ceil(2 * H / d)))
+    return O.Grid(Nx, Nt, Nt, d, d, d, -(R0 - L / 2) - Nx * d, -Nt * d / 2, -Nt * d / 2, C), m
+
+
 def debye_focal_field(theta0, truncated):
     """|E_y| at the focus from Debye's integral, with E0 from the printed
     normalisation (power P0 through the sphere) and F by quadrature."""
@@ -57,12 +81,8 @@ def debye_focal_field(theta0, truncated):
     A = np.exp(-a * a / theta0 ** 2)
     if truncated:
         A = A * edge_window(a, 2 * theta0, EPS)
-    phi = np.linspace(0.0, 2 * math.pi, 721)[:-1]
-    s_coarse = np.sin(a[::400])
-    pol = np.sqrt(1.0 - np.outer(s_coarse ** 2, np.cos(phi) ** 2)).mean(axis=1)
-    pol = np.interp(a, a[::400], pol)
     k = 2 * math.pi / LAM
-    return k * R0 * E0 * np.trapezoid(A * pol * np.sin(a), a)
+    return k * R0 * E0 * np.trapezoid(A * polarisation_average(a) * np.sin(a), a)
 
 
 def oracle_focal_field(fnum, ppl=6):
@@ -70,13 +90,7 @@ def oracle_focal_field(fnum, ppl=6):
     mapped layer, one exact step, sampling at the origin; the carrier amplitude
     from two samples a quarter period apart."""
     theta0 = O.theta_from_fnumber(fnum)
-    L = 4.5 * N_CYCLES * LAM
-    m = O.Mapping(R0, L)
-    D = O.d_min(R0, L, 2 * theta0 + EPS) + LAM
-    H = m.R_max * math.sin(2 * theta0 + EPS / 2) + LAM
-    d = LAM / ppl
-    Nx, Nt = smooth235(int(math.ceil(D / d))), smooth235(int(math.ceil(2 * H / d)))
-    g = O.Grid(Nx, Nt, Nt, d, d, d, -(R0 - L / 2) - Nx * d, -Nt * d / 2, -Nt * d / 2, C)
+    g, m = layer_grid(2 * theta0 + EPS / 2, R0, 4.5 * N_CYCLES * LAM, ppl)
     p = O.Pulse(kind=O.GAUSSIAN, lam=LAM, theta=theta0, eps=EPS, P0=P0, n_cycles=N_CYCLES)
     f0 = O.init_fields(g, m, p)
     T = R0 / C
@@ -102,3 +116,20 @@ def test_gaussian_focus_matches_debye_integral_and_paraxial_limit():
     # and the oracle's intensity sits just below I0, by the edge at 2 theta0
     ratio = (E[1] / E_par) ** 2
     assert 0.9 < ratio < 1.0
+
+
+def test_flat_top_tight_focus_matches_debye_integral():
+    """The paper's tight-focusing case (Sec. 3.1: f = 0.3, theta ~ 1 rad,
+    R0 = 16 lambda, L = 2 lambda, eps = 0.1), far from the paraxial regime."""
+    fnum, R0f, L = 0.3, 16.0, 2.0
+    theta = math.atan(1.0 / (2 * fnum))
+    g, m = layer_grid(theta + EPS / 2, R0f, L)
+    p = O.Pulse(kind=O.FLAT_TOP, lam=LAM, theta=theta, eps=EPS, P0=P0)
+    T = R0f / C
+    E = O.sample_plane(O.advance_exact(O.init_fields(g, m, p), g, T), g, m, 0.0, np.array([0.0]),
+                       np.array([0.0]), T)[:, 0, 0].real
+    a = np.linspace(0.0, math.pi, 400001)
+    A = math.sqrt(4 * P0 / (C * (1 - math.cos(theta))))          # Eq. 9
+    Ed = 2 * math.pi / LAM * A * np.trapezoid(edge_window(a, theta, EPS) * polarisation_average(a) * np.sin(a), a)
+    assert abs(E[0]) < 1e-5 * abs(E[1]) and abs(E[2]) < 1e-5 * abs(E[1])
+    assert abs(abs(E[1]) / Ed - 1.0) < 2e-3
