@@ -88,11 +88,12 @@ def dist_env():
     return RP.env()
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one ncu capture at 256^3 (mean of the forward and
-# inverse launches), keyed by (kernel, size, storage); to be re-taken whenever
-# that kernel changes.
-NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.69e6, ("plane_xy", 256, "real"): 750.11e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# step kernel kind, from one ncu capture at 256^3 (the plane kernels: mean of
+# the forward and inverse launches), keyed by (kernel, size, storage); to be
+# re-taken whenever that kernel changes.
+NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.69e6, ("plane_xy", 256, "real"): 750.11e6,
+                     ("kspace_z", 256, "complex"): 1621.73e6, ("kspace_z", 256, "real"): 822.44e6}
 
 
 def measured_peaks():
@@ -544,7 +545,11 @@ def step_roofline(prof, g, storage, size, peak, peak_src):
     hbm = {"algorithmic_bytes_per_cell_step": sweep_bytes / n_st / g.cells,
            "achieved_GBps": sweep_bytes / (step_total / 1e3) / 1e9,
            "frac_of_measured_peak": sweep_bytes / (step_total / 1e3) / 1e9 / peak,
-           "ms_per_psatd_step": step_total / n_st}
+           "ms_per_psatd_step": step_total / n_st,
+           "kernels": {k: {"avg_launch_ms": ms / n, "achieved_GBps": bytes_per_launch / (ms / n / 1e3) / 1e9,
+                           "frac": bytes_per_launch / (ms / n / 1e3) / 1e9 / peak,
+                           "traffic": NCU_TRAFFIC_BYTES.get((k, size, storage)), "launches": n}
+                       for k, (ms, n) in step_k.items() if n > 0}}
     return roof, hbm
 
 
