@@ -20,6 +20,9 @@ For a pulse of any duration the time-domain form of the same integral gives
 the field at the focus at t = R0/c from the slope of the longitudinal profile at
 its centre: u_l(s) = sin(k s) cos^2(pi s / L) of Eq. 7 has slope k there, so the
 flat-top pulse of Eq. 8-9 reaches |E_y(0)| = k A int u_ts sqrt(...) sin alpha.
+B = u s1 with s1 = d x R^ / |d x R^| has z component cos alpha / sqrt(1 - R^_y^2),
+so B_z(0) = k A int u_ts <cos alpha / sqrt(1 - sin^2 alpha cos^2 phi)>_phi
+sin alpha, with the sign of E_y for a converging pulse (E x B along +x there).
 
 For the untruncated Gaussian A = exp(-alpha^2/theta0^2) and small theta0 this
 tends to the paraxial focus I0 = 2 P0 / (pi w0^2), w0 = 2 f lambda / pi, that
@@ -53,11 +56,13 @@ def edge_window(alpha, theta, eps):
     return np.where(alpha <= theta - eps / 2, 1.0, np.where(alpha <= theta + eps / 2, ramp, 0.0))
 
 
-def polarisation_average(a):
-    """<sqrt(1 - sin^2 a cos^2 phi)>_phi: the y component of s0 averaged over phi."""
+def polarisation_average(a, component="E"):
+    """Over phi: <sqrt(1 - sin^2 a cos^2 phi)> (y component of s0, "E") or
+    <cos a / sqrt(1 - sin^2 a cos^2 phi)> (z component of s1, "B"; a < pi/2)."""
     phi = np.linspace(0.0, 2 * math.pi, 721)[:-1]
     coarse = a[::400]
-    pol = np.sqrt(1.0 - np.outer(np.sin(coarse) ** 2, np.cos(phi) ** 2)).mean(axis=1)
+    q = np.sqrt(1.0 - np.outer(np.sin(coarse) ** 2, np.cos(phi) ** 2))
+    pol = (q if component == "E" else np.cos(coarse)[:, None] / q).mean(axis=1)
     return np.interp(a, coarse, pol)
 
 
@@ -126,10 +131,16 @@ def test_flat_top_tight_focus_matches_debye_integral():
     g, m = layer_grid(theta + EPS / 2, R0f, L)
     p = O.Pulse(kind=O.FLAT_TOP, lam=LAM, theta=theta, eps=EPS, P0=P0)
     T = R0f / C
-    E = O.sample_plane(O.advance_exact(O.init_fields(g, m, p), g, T), g, m, 0.0, np.array([0.0]),
-                       np.array([0.0]), T)[:, 0, 0].real
-    a = np.linspace(0.0, math.pi, 400001)
+    EB = O.sample_plane(O.advance_exact(O.init_fields(g, m, p), g, T), g, m, 0.0, np.array([0.0]),
+                        np.array([0.0]), T, comps=(0, 1, 2, 3, 4, 5))[:, 0, 0].real
+    E, B = EB[:3], EB[3:]
+    a = np.linspace(0.0, theta + EPS / 2, 400001)                 # the support of u_ts
     A = math.sqrt(4 * P0 / (C * (1 - math.cos(theta))))          # Eq. 9
-    Ed = 2 * math.pi / LAM * A * np.trapezoid(edge_window(a, theta, EPS) * polarisation_average(a) * np.sin(a), a)
+    w = edge_window(a, theta, EPS) * np.sin(a)
+    Ed = 2 * math.pi / LAM * A * np.trapezoid(w * polarisation_average(a, "E"), a)
+    Bd = 2 * math.pi / LAM * A * np.trapezoid(w * polarisation_average(a, "B"), a)
     assert abs(E[0]) < 1e-5 * abs(E[1]) and abs(E[2]) < 1e-5 * abs(E[1])
     assert abs(abs(E[1]) / Ed - 1.0) < 2e-3
+    # B is along z with E_y's sign, and smaller than E_y at this focusing (Bd / Ed = 0.97)
+    assert abs(B[0]) < 1e-5 * abs(B[2]) and abs(B[1]) < 1e-5 * abs(B[2])
+    assert B[2] * E[1] > 0 and abs(B[2] / Bd - 1.0) < 2e-3
