@@ -123,9 +123,10 @@ def test_gaussian_focus_matches_debye_integral_and_paraxial_limit():
     assert 0.9 < ratio < 1.0
 
 
-def test_flat_top_tight_focus_matches_debye_integral():
+def flat_top_focus_checks():
     """The paper's tight-focusing case (Sec. 3.1: f = 0.3, theta ~ 1 rad,
-    R0 = 16 lambda, L = 2 lambda, eps = 0.1), far from the paraxial regime."""
+    R0 = 16 lambda, L = 2 lambda, eps = 0.1), far from the paraxial regime:
+    each check of the focal E and B against the Debye integrals, by name."""
     fnum, R0f, L = 0.3, 16.0, 2.0
     theta = math.atan(1.0 / (2 * fnum))
     g, m = layer_grid(theta + EPS / 2, R0f, L)
@@ -139,8 +140,38 @@ def test_flat_top_tight_focus_matches_debye_integral():
     w = edge_window(a, theta, EPS) * np.sin(a)
     Ed = 2 * math.pi / LAM * A * np.trapezoid(w * polarisation_average(a, "E"), a)
     Bd = 2 * math.pi / LAM * A * np.trapezoid(w * polarisation_average(a, "B"), a)
-    assert abs(E[0]) < 1e-5 * abs(E[1]) and abs(E[2]) < 1e-5 * abs(E[1])
-    assert abs(abs(E[1]) / Ed - 1.0) < 2e-3
-    # B is along z with E_y's sign, and smaller than E_y at this focusing (Bd / Ed = 0.97)
-    assert abs(B[0]) < 1e-5 * abs(B[2]) and abs(B[1]) < 1e-5 * abs(B[2])
-    assert B[2] * E[1] > 0 and abs(B[2] / Bd - 1.0) < 2e-3
+    return {
+        "E along y": abs(E[0]) < 1e-5 * abs(E[1]) and abs(E[2]) < 1e-5 * abs(E[1]),
+        "E_y = Debye": abs(abs(E[1]) / Ed - 1.0) < 2e-3,
+        # B is along z with E_y's sign, and smaller than E_y at this focusing (Bd / Ed = 0.97)
+        "B along z": abs(B[0]) < 1e-5 * abs(B[2]) and abs(B[1]) < 1e-5 * abs(B[2]),
+        "B_z = Debye, sign of E_y": bool(B[2] * E[1] > 0) and abs(B[2] / Bd - 1.0) < 2e-3,
+    }
+
+
+def test_flat_top_tight_focus_matches_debye_integral():
+    checks = flat_top_focus_checks()
+    assert all(checks.values()), checks
+
+
+def test_focus_checks_catch_planted_mistakes(monkeypatch):
+    """Plausible mistakes in the amplitude, the polarisation and the mapping
+    each fail at least one of the focus checks."""
+    good_A, good_pol, good_T = O.flat_top_A, O.polarisation_vectors, O.mapping_T
+
+    def A_wrong_sign(P0_, c, theta):           # 1 + cos theta in Eq. 9
+        return math.sqrt(4.0 * P0_ / (c * (1.0 + math.cos(theta))))
+
+    def B_reversed(X, Y, Z, d):                # s1 = R x d: a diverging pulse
+        s0, s1 = good_pol(X, Y, Z, d)
+        return s0, -s1
+
+    def T_half_period(x, x_min, D):            # Eq. 13 off by half a period
+        return good_T(np.asarray(x) + D / 2, x_min, D)
+
+    for name, plant in (("flat_top_A", A_wrong_sign), ("polarisation_vectors", B_reversed),
+                        ("mapping_T", T_half_period)):
+        monkeypatch.setattr(O, name, plant)
+        assert not all(flat_top_focus_checks().values()), name
+        monkeypatch.setattr(O, name, {"flat_top_A": good_A, "polarisation_vectors": good_pol,
+                                      "mapping_T": good_T}[name])
