@@ -262,11 +262,14 @@ psatd_status psatd_selftest_wait_timeout(psatd_ctx* ctx);
  * 6 * n_cells complex values of the given precision (32 or 64); out receives
  * {energy_E, energy_B}, on the device (out_on_device != 0, asynchronous on
  * cuda_stream) or on the host (the call then synchronises the stream).  The
- * first call on each device looks up the array's device address (no
- * allocation); make that first call before any stream capture.  All calls share
- * the array, so calls that overlap on the GPU race and must be serialised by the
- * caller.  Needs no context; errors are returned only as the status.  The paper
- * has no counterpart. */
+ * first call on each device looks up the array's device address and loads the
+ * entry point's kernels for both precisions (the runtime would otherwise load
+ * each kernel on its first launch, which can allocate); make that first call
+ * before any stream capture.  After it, no call on that device allocates.  All
+ * calls share the array, so calls that overlap on the GPU race and must be
+ * serialised by the caller.  Needs no context; errors are returned only as the
+ * status, and a launch failure is reported from the launch itself: an error the
+ * caller left pending is not consumed.  The paper has no counterpart. */
 psatd_status psatd_energy_noalloc(const void* fields, int precision, long long n_cells, double* out,
                                   int out_on_device, void* cuda_stream);
 

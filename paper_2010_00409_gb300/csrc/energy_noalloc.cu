@@ -15,7 +15,8 @@
 // GPU that loads the library holds the array until the process exits.  All calls
 // share it: each call overwrites every partial it reads, so nothing needs
 // clearing, but two calls whose kernels overlap on a GPU (different streams)
-// race on it and must be serialised by the caller.
+// race on it and must be serialised by the caller.  The first call on a device
+// also loads the three kernels, so that no later call allocates.
 #include <mutex>
 
 #include "../../include/psatd.h"
@@ -108,9 +109,16 @@ extern "C" psatd_status psatd_energy_noalloc(const void* fields, int precision, 
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
         if (!g_scratch_addr[dev]) {
+            // The runtime loads kernels lazily, and loading one can allocate
+            // device memory; load all three here so that no later call, of
+            // either precision, does.
+            cudaFuncAttributes fa;
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_energy_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
+            if (cudaFuncGetAttributes(&fa, energy_partials_kernel<float>) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, energy_partials_kernel<double>) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, energy_final_kernel) != cudaSuccess ||
+                cudaGetSymbolAddress(&p, g_energy_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();                        // clear this call's own failure
                 return PSATD_ERR_CUDA;
             }
             g_scratch_addr[dev] = static_cast<double*>(p);
@@ -118,15 +126,18 @@ extern "C" psatd_status psatd_energy_noalloc(const void* fields, int precision, 
         scratch = g_scratch_addr[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    if (precision == 64)
-        energy_partials_kernel<double><<<(unsigned)nparts, kThreads, 0, s>>>(
-            static_cast<const cplx<double>*>(fields), n_cells, scratch);
-    else
-        energy_partials_kernel<float><<<(unsigned)nparts, kThreads, 0, s>>>(
-            static_cast<const cplx<float>*>(fields), n_cells, scratch);
+    // cudaLaunchKernel returns this launch's own error: an error that the
+    // caller left pending is neither consumed nor reported here
+    int np = (int)nparts;
     double* result = out_on_device ? out : scratch + 2 * (size_t)kMaxPartials;
-    energy_final_kernel<<<1, kThreads, 0, s>>>(scratch, (int)nparts, result);
-    if (cudaGetLastError() != cudaSuccess) return PSATD_ERR_CUDA;
+    void* args_p[] = {const_cast<void**>(&fields), &n_cells, &scratch};
+    const void* kp = precision == 64 ? (const void*)energy_partials_kernel<double>
+                                     : (const void*)energy_partials_kernel<float>;
+    if (cudaLaunchKernel(kp, dim3((unsigned)nparts), dim3(kThreads), args_p, 0, s) != cudaSuccess)
+        return PSATD_ERR_CUDA;
+    void* args_f[] = {&scratch, &np, &result};
+    if (cudaLaunchKernel((const void*)energy_final_kernel, dim3(1), dim3(kThreads), args_f, 0, s) != cudaSuccess)
+        return PSATD_ERR_CUDA;
     if (!out_on_device) {
         if (cudaMemcpyAsync(out, result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return PSATD_ERR_CUDA;

@@ -50,3 +50,31 @@ def test_energy_noalloc_rejects_sizes_beyond_its_array(lib):
     assert L.psatd_energy_noalloc(C.c_void_p(256), 32, (1 << 30) + 1, host, 0, None) == lib.ERR_SIZE
     assert L.psatd_energy_noalloc(C.c_void_p(256), 32, 0, host, 0, None) == lib.ERR_SIZE
     assert L.psatd_energy_noalloc(C.c_void_p(256), 16, 10, host, 0, None) == lib.ERR_ARG
+
+
+def test_energy_noalloc_allocates_nothing_after_its_first_call(lib):
+    """After one call (of either precision) on a device, calls of both
+    precisions leave the device's free memory unchanged: the first call loads
+    every kernel of the entry point."""
+    import torch
+    L = lib.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 40 * 48 * 64
+    f32 = torch.ones((6, n), dtype=torch.complex64, device=dev)
+    f64 = torch.ones((6, n), dtype=torch.complex128, device=dev)
+    out = torch.zeros(2, dtype=torch.float64, device=dev)
+    pout = C.cast(C.c_void_p(out.data_ptr()), C.POINTER(C.c_double))
+    s = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    host = (C.c_double * 2)()
+    assert L.psatd_energy_noalloc(C.c_void_p(f32.data_ptr()), 32, n, host, 0, s) == lib.OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for _ in range(2):
+        for prec, f in ((64, f64), (32, f32)):
+            assert L.psatd_energy_noalloc(C.c_void_p(f.data_ptr()), prec, n, pout, 1, s) == lib.OK
+            torch.cuda.synchronize()
+            assert out.cpu().numpy().tolist() == [3.0 * n, 3.0 * n]
+            assert L.psatd_energy_noalloc(C.c_void_p(f.data_ptr()), prec, n, host, 0, s) == lib.OK
+            assert [host[0], host[1]] == [3.0 * n, 3.0 * n]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
