@@ -20,6 +20,13 @@ namespace psatd {
 
 namespace {
 
+// L2 prefetch distance in tiles (0: none): thread 0 of the block on field tile
+// bt asks L2 for the six component boxes of tile bt + kKsPf.
+#ifndef PSATD_KS_PF
+#define PSATD_KS_PF 152
+#endif
+constexpr int kKsPf = PSATD_KS_PF;
+
 // Barrier over the NT threads of group h only (named barrier 1 + h; barrier 0
 // is __syncthreads): the exchange rounds of a group touch only its own
 // components' slots, so the other group need not wait.
@@ -121,6 +128,11 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
             mbar_arrive_expect_tx(&bar[q], kBytes / 6);
             if (nq) tma_load_3d(spec + q * SLOT, &map_nyq, &bar[q], bt * W * xw, 0, q);
             else tma_load_4d(spec + q * SLOT, &map, &bar[q], xt * W * xw, y, 0, q);
+        }
+        if constexpr (kKsPf > 0) {
+            const int bn = bt + kKsPf;
+            if (!nq && bn < ntile * Ny)
+                for (int q = 0; q < 6; ++q) tma_prefetch_4d(&map, (bn % ntile) * W * xw, bn / ntile, 0, q);
         }
     }
 

@@ -41,6 +41,7 @@
 #include <cooperative_groups.h>
 
 #include "fft_reg.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -57,6 +58,30 @@ __device__ __forceinline__ int sw16(int row, int col) { return row * 16 + (col ^
 
 constexpr int owner_of(int k1) { return (k1 == 0 || k1 == 8) ? 0 : (k1 < 8 ? k1 : 16 - k1); }
 constexpr int half_of(int k1) { return (k1 == 0) ? 0 : (k1 == 8 ? 1 : (k1 < 8 ? 0 : 1)); }
+
+// Field loads and stores of the plane kernels.  Each field value is read once
+// and written once per launch.
+#ifndef PSATD_RC_LD
+#define PSATD_RC_LD 0
+#endif
+__device__ __forceinline__ float2 ld_field(const float2* p) {
+#if PSATD_RC_LD == 1
+    return __ldcs(p);
+#elif PSATD_RC_LD == 2
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ void st_field(float2* p, float2 v) {
+#if PSATD_RC_LD >= 1
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
 
 // W_256^k for compile-time k
 template <int K> __device__ __forceinline__ float2 w256() {
@@ -175,7 +200,7 @@ __device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, i
         float2* out = plane + 16 * r + c;
         static_for<0, 16>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
-            out[(size_t)(jy + 16 * k2) * kM] = v[k2];
+            st_field(out + (size_t)(jy + 16 * k2) * kM, v[k2]);
         });
     }
 }
@@ -266,13 +291,36 @@ __device__ __forceinline__ void c2r_stage_a_store(const float2* tile, int r, int
     static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[decltype(kc)::value * 256 + j * 32 + (yl ^ j)]; });
     reg_dft<float, +1, 16>(v);                         // v[n1] = z[j + 8 n1]
     float2* p = plane + (size_t)(32 * r + yl) * kM;
-    static_for<0, 16>([&](auto nc) { p[j + 8 * decltype(nc)::value] = v[decltype(nc)::value]; });
+    static_for<0, 16>([&](auto nc) { st_field(p + j + 8 * decltype(nc)::value, v[decltype(nc)::value]); });
 }
 
 constexpr size_t kTileBytes = (size_t)kM * kNy / kRcC * sizeof(float2);   // 32 KB
 
+// L2 prefetch distance in planes (0: none).  Block r of the cluster on plane pl
+// asks L2 for its 32 KB share of plane pl + kPlanePf, so that the cluster that
+// takes that plane about one block lifetime later finds its input in L2.
+#ifndef PSATD_PLANE_PF
+#define PSATD_PLANE_PF 20
+#endif
+constexpr int kPlanePf = PSATD_PLANE_PF;
+
+__device__ __forceinline__ void prefetch_plane(const float2* data, int pl, int r) {
+    if constexpr (kPlanePf > 0) {
+        const int npl = (int)(gridDim.x / kRcC);
+        if (threadIdx.x == 0 && pl + kPlanePf < npl)
+            prefetch_l2_bulk(data + (size_t)(pl + kPlanePf) * (kM * kNy) + (size_t)r * (kTileBytes / sizeof(float2)),
+                             (uint32_t)kTileBytes);
+    }
+}
+
 // 64 registers: four blocks per SM
-__global__ void __launch_bounds__(kRcThreads)
+#ifndef PSATD_RC_MINB_R2C
+#define PSATD_RC_MINB_R2C 4
+#endif
+#ifndef PSATD_RC_MINB_C2R
+#define PSATD_RC_MINB_C2R 5
+#endif
+__global__ void __launch_bounds__(kRcThreads, PSATD_RC_MINB_R2C)
 plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
                  float2* __restrict__ nyq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -287,13 +335,14 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     float2* plane = data + (size_t)pl * (kM * kNy);
     const int tid = threadIdx.x;
     pdl_wait();
+    prefetch_plane(data, pl, r);
 
     {
         const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
         const int y = 32 * r + w + 8 * g;              // rows of a warp alternate in bit 3 (bank spread)
         const float2* p = plane + (size_t)y * kM;
         float2 v[16];
-        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = p[j + 8 * decltype(nc)::value]; });
+        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = ld_field(p + j + 8 * decltype(nc)::value); });
         r2c_stage_a(v, j, twx);
         cluster.barrier_wait();
         r2c_scatter(v, cluster, tile, y, j);
@@ -304,7 +353,7 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
 
 // capped at 48 registers: five blocks per SM (the packed butterfly adds would
 // otherwise take it to 54 registers and four blocks)
-__global__ void __launch_bounds__(kRcThreads, 5)
+__global__ void __launch_bounds__(kRcThreads, PSATD_RC_MINB_C2R)
 plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, const float2* __restrict__ twy,
                  const float2* __restrict__ nyq) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -317,12 +366,13 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     float2* plane = data + (size_t)pl * (kM * kNy);
     const int tid = threadIdx.x;
     pdl_wait();
+    prefetch_plane(data, pl, r);
 
     {
         const int c = tid & 15, jy = tid >> 4;
         const float2* in = plane + 16 * r + c;
         float2 v[16];
-        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = in[(size_t)(jy + 16 * decltype(kc)::value) * kM]; });
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = ld_field(in + (size_t)(jy + 16 * decltype(kc)::value) * kM); });
         c2r_columns(v, tile, r, c, jy, twy, nyq + (size_t)pl * kNy);
     }
     __syncthreads();
