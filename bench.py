@@ -21,7 +21,8 @@ Beside the headline (N = 1 only where noted) the line carries: the other field
 storage, `e2e` (host buffers through the C ABI), `fp64` (the plain float64
 solver, with its arithmetic roofline against the float64 FMA rate measured in
 the same run), `focal_forms` (one-shot against stepped focal fields), `batched_sweep`
-(64 realisations as one CUDA graph), `multi_octave` (the 1024^3 float32
+(64 realisations as one CUDA graph of one-shots), `batched_stepped` (the same 64
+realisations stepped to their foci by one persistent launch), `multi_octave` (the 1024^3 float32
 multi-octave layer against float64 at 768^3; --multi-octave-steps 0 steps it to
 the focus), `surrogate_gemm` (the tensor-core GEMM), `cufft_reference` (cuFFT
 through torch.fft as a library reference), `cpu_baseline` (the oracle on one
@@ -67,6 +68,7 @@ def args_parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-stepped-sweep", action="store_true")
     ap.add_argument("--no-multi-octave", action="store_true")
     ap.add_argument("--no-gemm", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
@@ -327,6 +329,8 @@ def run_ours(a):
     ctx.close()
     if not a.no_sweep:
         line["batched_sweep"] = sweep_measure(dev, stream)
+    if not a.no_stepped_sweep and world == 1:
+        line["batched_stepped"] = stepped_sweep_measure(dev, stream)
     if not a.no_multi_octave and world == 1:
         line["multi_octave"] = multi_octave_measure(dev, stream, k=a.multi_octave_steps)
     if not a.no_gemm and world == 1:
@@ -739,6 +743,108 @@ def sweep_measure(dev, stream, n=64, reps=3, n_check=4):
     for c, *_ in items:
         c.close()
     return res
+
+
+def stepped_sweep_measure(dev, stream, n=64, n_check=4, k_steps=4, fp64_boxes=4, fp64_steps=4):
+    """The sweep realisations (seeded CEP, ellipticity, f-number; 11 uneven grid
+    shapes, 96-192 per axis, complex float32) stepped to their foci: each box is
+    initialised on its layer (pulse + projection), ALL boxes are advanced by one
+    persistent launch (psatd_multi_advance; box p takes ceil(T_p / dt_C,p) steps
+    of T_p / that count, T_p = R0/c), then each focal plane (64 x 64) is
+    sampled.  focal_fields_per_s = n / (init + launch + sampling).  Radix
+    schedules and tile widths come from psatd_multi_autotune (its time is
+    reported apart).  Beside it, over k_steps steps of all boxes: the same boxes
+    stepped one context after another (the library's per-box launches), and the
+    plain float64 stepped solver on fp64_boxes boxes (whole-job rate scaled from
+    fp64_steps timed steps plus its init and sampling).  Errors: float32
+    stepped focal planes against float64 one-shots (one exact step of T_p) of
+    the first n_check realisations."""
+    import torch
+    from paper_2010_00409_gb300 import psatd
+    sweep = W.batched_sweep(n, seed=0)
+    items, steps = [], []
+    for g, m, p, T, plane in sweep:
+        k = math.ceil(T / g.courant_dt())
+        c = psatd.Context(g, m, T / k, 32, stream=stream)
+        o = torch.empty((3, plane["nz"], plane["ny"]), dtype=torch.complex64, device=dev)
+        args = (plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])
+        items.append((c, p, args, o))
+        steps.append(k)
+    ctxs = [it[0] for it in items]
+    for c, p, _, _ in items:
+        c.init_pulse(p)
+    t_tune = time.perf_counter()
+    ms_tuned = psatd.multi_autotune(ctxs, 1)
+    t_tune = time.perf_counter() - t_tune
+
+    def job():
+        for c, p, _, _ in items:
+            c.init_pulse(p)
+        psatd.multi_advance(ctxs, steps)
+        for c, _, args, o in items:
+            c.sample_focal_plane(*args, out=o)
+
+    job()
+    ctxs[0].synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    job()
+    e1.record(stream)
+    e1.synchronize()
+    ctxs[0].synchronize()                      # no barrier wait expired
+    ms_job = e0.elapsed_time(e1)
+    errs = []
+    for (g, m, p, T, plane), (c, _, args, o) in zip(sweep[:n_check], items[:n_check]):
+        with psatd.Context(g, m, T / 100, 64, stream=stream) as c64:
+            w = c64.focal_one_shot(p, T, *args)
+        errs.append(float(np.linalg.norm(o.cpu().numpy() - w) / np.linalg.norm(w)))
+    # per batched step: one persistent launch against per-context launches
+    e0.record(stream)
+    psatd.multi_advance(ctxs, k_steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_multi = e0.elapsed_time(e1) / k_steps
+    n_launch0 = sum(c.launch_count for c in ctxs)
+    e0.record(stream)
+    for c in ctxs:
+        c.advance(k_steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_eager = e0.elapsed_time(e1) / k_steps
+    eager_launches = (sum(c.launch_count for c in ctxs) - n_launch0) / k_steps
+    cells = sum(g.cells for g, *_ in sweep)
+    # the plain float64 stepped solver on the first fp64_boxes boxes
+    t64 = 0.0
+    for (g, m, p, T, plane), k in zip(sweep[:fp64_boxes], steps[:fp64_boxes]):
+        with psatd.Context(g, m, T / k, 64, stream=stream) as c64:
+            args = (plane["x_p"], plane["ny"], plane["nz"], plane["y0"], plane["y1"], plane["z0"], plane["z1"])
+            c64.init_pulse(p)
+            c64.advance(1)
+            c64.synchronize()
+            a0, a1, a2, a3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            a0.record(stream)
+            c64.init_pulse(p)
+            a1.record(stream)
+            c64.advance(fp64_steps)
+            a2.record(stream)
+            c64.sample_focal_plane(*args)
+            a3.record(stream)
+            a3.synchronize()
+            t_step = a1.elapsed_time(a2) / fp64_steps
+            t64 += (a0.elapsed_time(a1) + k * t_step + a2.elapsed_time(a3)) / 1e3
+    for c in ctxs:
+        c.close()
+    return {"realisations": n, "grid_shapes": len({(g.Nx, g.Ny, g.Nz) for g, *_ in sweep}),
+            "steps_min_max": [min(steps), max(steps)], "cells_total": cells,
+            "focal_fields_per_s": n / (ms_job / 1e3), "ms_per_batch_job": ms_job,
+            "launches_per_batch_advance": 1,
+            "ms_per_batched_step_persistent": ms_multi, "ms_per_batched_step_eager_per_context": ms_eager,
+            "eager_launches_per_batched_step": eager_launches,
+            "cell_steps_per_s_persistent": cells / (ms_multi / 1e3),
+            "autotune_s": t_tune, "autotune_best_ms_per_step": ms_tuned,
+            "fp64_stepped_focal_fields_per_s": fp64_boxes / t64,
+            "fp64_rate_from": "%d boxes, %d timed steps each scaled to the box's step count" % (fp64_boxes, fp64_steps),
+            "max_rel_l2_err_fp32_stepped_vs_fp64_exact": max(errs), "err_checked_on": n_check}
 
 
 def main():

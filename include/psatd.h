@@ -290,6 +290,42 @@ psatd_status psatd_batch_launch(psatd_batch* batch);
 long long psatd_batch_nodes(const psatd_batch* batch);      /* graph nodes, 0 if none */
 void psatd_batch_destroy(psatd_batch* batch);
 
+/* Persistent batched advance (the parameter sweeps of Sec. 3.2.3: statistics
+ * over many perturbed pulse realisations, each on its own periodic layer of
+ * Sec. 2.3).  Advances context ctxs[p] by n_steps[p] >= 0 PSATD steps of its
+ * own dt (Sec. 2.1, Eq. 3-4), for all p < n_ctx, in ONE cooperative kernel
+ * launch on the stream of ctxs[0] that runs the largest count (a box past its
+ * own count skips its work): each step is five phases (x, y, the fused z pass with the
+ * update, y inverse, x inverse), each a list of work items over all boxes, with
+ * a grid-wide barrier between phases.  The contexts need complex field storage
+ * (not PSATD_FLAG_REAL_FIELDS), one precision, one device and one stream,
+ * distinct field storage and axis lengths up to 1024; grids may all differ.
+ * Each barrier wait is bounded (2 s): if one expires the blocks leave the
+ * kernel, the boxes' fields are invalid, and the next psatd_synchronize of
+ * ctxs[0] returns PSATD_ERR_TIMEOUT.  Radix schedules and tile widths come from
+ * psatd_multi_autotune when it has run for the axis lengths, else defaults.
+ * Asynchronous; recorded into a batch capture when ctxs[0]'s stream is being
+ * captured (the same boxes with the same step counts must have been advanced
+ * once before the capture: that call uploads their descriptors).  Errors are reported through ctxs[0] (psatd_last_error). */
+psatd_status psatd_multi_advance(psatd_ctx* const* ctxs, int n_ctx, const int* n_steps);
+
+/* Autotuner of the batched advance: on copies of the fields (the contexts'
+ * fields are left unchanged), times trial_steps steps of the whole batch for
+ * every distinct radix schedule (radices 8/4/5/3/2 or 4/5/3/2, largest or
+ * smallest first) and tile-width scale (1/2, 1, 2) of each axis length in turn
+ * (coordinate descent), keeps the fastest and caches it per (precision, axis
+ * length) for later psatd_multi_advance calls in this process.  Writes the best
+ * time per step.  Synchronises the stream; needs memory for one copy of all
+ * the fields (PSATD_ERR_OOM otherwise, nothing changed). */
+psatd_status psatd_multi_autotune(psatd_ctx* const* ctxs, int n_ctx, int trial_steps, double* ms_per_step);
+
+/* Self-test of the batched advance's bounded grid barrier: launches it on this
+ * context with one arrival more than the grid can give, so every block's first
+ * barrier wait expires after 2 ms; returns what psatd_synchronize reports
+ * (PSATD_ERR_TIMEOUT when the bound works).  The field content is undefined
+ * afterwards; the context stays usable.  The paper has no counterpart. */
+psatd_status psatd_selftest_grid_barrier_timeout(psatd_ctx* ctx);
+
 /* Autotuner: times trial_steps PSATD steps of each kernel path (AUTO, REGISTER,
  * GENERIC) and generic tile width scale (1/2, 1, 2) on a scratch copy of the
  * field, keeps the fastest for this context and caches it per grid shape and

@@ -147,6 +147,37 @@ template <typename T> struct Tables {
     int tile_shift = 0;         // generic kernels: tile width scaled by 2^tile_shift (autotuner)
 };
 
+// One periodic box of a persistent batched advance (multi_advance.cu): its
+// complex fields [6][Nz][Ny][Nx], tables, the radix schedule of each axis and
+// the tile widths of the x (rows per tile), y and z (x-columns per tile) phases.
+template <typename T> struct MultiProblem {
+    cplx<T>* f;
+    const cplx<T>* tw[3];
+    const T* k[3];
+    const ModeCoef<T>* coef;
+    int N[3];
+    int W[3];
+    int nsteps;                 // this box's steps (the launch runs the largest count)
+    AxisPlan plan[3];
+};
+
+// Shared-memory bytes of one tile of the phase along `axis` (N_axis points,
+// W pencils): two Stockham buffers for x and y, six components and a partner
+// buffer for the fused z pass.
+template <typename T> size_t multi_tile_bytes(int axis, int N_axis, int W);
+
+// Persistent cooperative launch advancing nprob boxes by up to nsteps PSATD
+// steps (box p by its own probs[p].nsteps <= nsteps).
+// prefix[a][p] (a = 0, 1, 2; p = 0..nprob) are the first work items of box p in
+// the x, y and z phases; tile_bytes the largest tile; bar a device counter the
+// launch resets first; err the device error word; limit_ns the bound of each
+// barrier wait; extra > 0 makes every barrier unreachable (self-test of the
+// bounded wait).  The grid is the co-resident block count (at most max_items).
+template <typename T>
+cudaError_t launch_multi_advance(const MultiProblem<T>* probs, const long long* prefix, int nprob, int nsteps,
+                                 size_t tile_bytes, long long max_items, unsigned* bar, int* err,
+                                 unsigned long long limit_ns, unsigned extra, cudaStream_t s, int* grid_out);
+
 // K2 modes: ROTATE = full step (forward z, update, inverse z); PROJECT = the
 // one-time transverse projection; ROTATE_SPECTRAL = forward z and update only,
 // leaving the spectrum (natural kx, ky, kz order) in storage.

@@ -11,12 +11,14 @@
 #include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
 
 #include "../../include/psatd.h"
 #include "common.cuh"
+#include "tma.cuh"
 
 using namespace psatd;
 
@@ -123,6 +125,11 @@ struct psatd_ctx {
     bool coef_T_ok = false;
     DevBuf coef_proj;                   // C = 1/Ntot, S = 0: the projection through the TMA kernel
     bool holds_spectrum = false;
+
+    // persistent batched advance led by this context: barrier counter, work
+    // prefix and box descriptors on the device, and the bytes last uploaded
+    DevBuf multi;
+    std::vector<unsigned char> multi_sig;
     std::string err = "no error";
 
     // per-kernel event timing (psatd_profile_enable)
@@ -395,6 +402,9 @@ psatd_status check_device_error(psatd_ctx* c) {
     if (h) {
         CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
+        if (h & DEV_ERR_GRID_TIMEOUT)
+            return fail(c, PSATD_ERR_TIMEOUT, "a bounded grid-barrier wait of the persistent batched advance expired; "
+                                              "the fields of its boxes are invalid");
         return fail(c, PSATD_ERR_TIMEOUT, "a bounded device wait for a tensor copy expired; results of that step are invalid");
     }
     return PSATD_OK;
@@ -636,6 +646,190 @@ cudaError_t one_shot_spectrum(psatd_ctx* c, bool project_b) {
     });
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent batched advance (multi_advance.cu)
+
+// Radix schedules the batch autotuner chooses from for an axis of N points:
+// 0 radices 8, 4, 5, 3, 2 largest first (make_plan), 1 the same radices smallest
+// first, 2 radices 4, 5, 3, 2 (no 8) largest first, 3 those smallest first.
+constexpr int kPlanVariants = 4;
+bool make_plan_variant(int N, int variant, AxisPlan* p) {
+    AxisPlan q;
+    q.N = N;
+    q.npass = 0;
+    int n = N;
+    static const int with8[5] = {8, 4, 5, 3, 2}, no8[4] = {4, 5, 3, 2};
+    const int* rs = (variant & 2) ? no8 : with8;
+    const int nr = (variant & 2) ? 4 : 5;
+    for (int i = 0; i < nr; ++i)
+        while (n % rs[i] == 0 && q.npass < kMaxPass) {
+            q.radix[q.npass++] = rs[i];
+            n /= rs[i];
+        }
+    if (n != 1) return false;
+    if (variant & 1) std::reverse(q.radix, q.radix + q.npass);
+    *p = q;
+    return true;
+}
+
+bool same_plan(const AxisPlan& a, const AxisPlan& b) {
+    if (a.N != b.N || a.npass != b.npass) return false;
+    for (int i = 0; i < a.npass; ++i)
+        if (a.radix[i] != b.radix[i]) return false;
+    return true;
+}
+
+// Shared-memory budget of one tile: four blocks of 256 threads per SM in
+// float32 (64 registers a thread), two in float64 (more registers).
+#ifndef PSATD_MULTI_BUDGET_F32
+#define PSATD_MULTI_BUDGET_F32 (56 * 1024)
+#endif
+template <typename T> constexpr size_t multi_tile_budget() {
+    return sizeof(T) == 4 ? (size_t)(PSATD_MULTI_BUDGET_F32) : (size_t)(100 * 1024);
+}
+constexpr size_t kMultiHeader = 256;              // barrier counter at the start of the batch buffer
+constexpr int kMultiMaxN = 1024;
+constexpr unsigned long long kMultiWaitNs = 2000000000ull;   // 2 s per barrier wait
+
+// tuned (radix schedule, tile-width scale) per (precision, axis length)
+struct MultiChoice {
+    int variant = 0, scale = 0;
+    bool operator==(const MultiChoice& o) const { return variant == o.variant && scale == o.scale; }
+};
+std::map<std::pair<int, int>, MultiChoice> g_multi_tuned;
+std::mutex g_multi_mutex;
+
+MultiChoice multi_choice(int prec, int N) {
+    std::lock_guard<std::mutex> lock(g_multi_mutex);
+    auto it = g_multi_tuned.find({prec, N});
+    return it == g_multi_tuned.end() ? MultiChoice{} : it->second;
+}
+
+// Tile width of the phase along `axis`: x rows (~2048 points per tile), y
+// x-columns (128 contiguous bytes per row), z x-columns (64 bytes, six
+// components held), scaled by 2^scale and halved until the tile fits.
+template <typename T>
+int multi_width(int axis, const psatd_grid& g, int scale) {
+    const int es = (int)sizeof(cplx<T>);
+    const int N = axis_n(g, axis);
+    int w = axis == 0 ? std::max(1, std::min(64, 2048 / std::max(N, 1))) : std::min(g.Nx, (axis == 1 ? 128 : 64) / es);
+    w = scale > 0 ? (w << scale) : (scale < 0 ? (w >> -scale) : w);
+    w = std::max(1, std::min(w, axis == 0 ? 128 : g.Nx));
+    while (w > 1 && multi_tile_bytes<T>(axis, N, w) > multi_tile_budget<T>()) w /= 2;
+    return w;
+}
+
+struct MultiPrepared {
+    const void* probs = nullptr;
+    const long long* prefix = nullptr;
+    unsigned* bar = nullptr;
+    size_t tile = 0;
+    long long max_items = 0;
+};
+
+// Describe the boxes (fields[p] replaces box p's storage when given), upload
+// the descriptors to the lead context's buffer when they changed, and return
+// the device pointers.  choice overrides the tuned schedules per axis length.
+template <typename T>
+psatd_status multi_prepare(psatd_ctx* const* ctxs, int n, const int* steps, void* const* fields,
+                           const std::map<int, MultiChoice>* choice, MultiPrepared* out) {
+    psatd_ctx* c0 = ctxs[0];
+    std::vector<MultiProblem<T>> probs((size_t)n);
+    std::vector<long long> prefix(3 * (size_t)(n + 1), 0);
+    size_t tile = 0;
+    for (int p = 0; p < n; ++p) {
+        psatd_ctx* c = ctxs[p];
+        MultiProblem<T>& P = probs[p];
+        std::memset(&P, 0, sizeof P);
+        P.f = static_cast<cplx<T>*>(fields ? fields[p] : c->fields);
+        P.coef = static_cast<const ModeCoef<T>*>(c->coef.p);
+        P.nsteps = steps[p];
+        for (int a = 0; a < 3; ++a) {
+            P.tw[a] = static_cast<const cplx<T>*>(c->tw[a].p);
+            P.k[a] = static_cast<const T*>(c->k[a].p);
+            P.N[a] = axis_n(c->grid, a);
+            MultiChoice ch = multi_choice(c->prec, P.N[a]);
+            if (choice) {
+                auto it = choice->find(P.N[a]);
+                if (it != choice->end()) ch = it->second;
+            }
+            if (!make_plan_variant(P.N[a], ch.variant, &P.plan[a])) make_plan(P.N[a], &P.plan[a]);
+            P.W[a] = multi_width<T>(a, c->grid, ch.scale);
+            tile = std::max(tile, multi_tile_bytes<T>(a, P.N[a], P.W[a]));
+        }
+        const long long Nx = P.N[0], Ny = P.N[1], Nz = P.N[2];
+        const long long items[3] = {(6 * Nz * Ny + P.W[0] - 1) / P.W[0], 6 * Nz * ((Nx + P.W[1] - 1) / P.W[1]),
+                                    Ny * ((Nx + P.W[2] - 1) / P.W[2])};
+        for (int a = 0; a < 3; ++a) prefix[a * (n + 1) + p + 1] = prefix[a * (n + 1) + p] + items[a];
+    }
+    long long max_items = 0;
+    for (int a = 0; a < 3; ++a) max_items = std::max(max_items, prefix[a * (n + 1) + n]);
+    const size_t pbytes = (prefix.size() * sizeof(long long) + 15) / 16 * 16;
+    const size_t dbytes = probs.size() * sizeof(MultiProblem<T>);
+    std::vector<unsigned char> sig(pbytes + dbytes, 0);
+    std::memcpy(sig.data(), prefix.data(), prefix.size() * sizeof(long long));
+    std::memcpy(sig.data() + pbytes, probs.data(), dbytes);
+    if (c0->multi.bytes < kMultiHeader + sig.size() || sig != c0->multi_sig) {
+        if (capturing(c0))
+            return fail(c0, PSATD_ERR_STATE, "inside a batch capture psatd_multi_advance needs the boxes, step counts "
+                                             "and tuning of a call made before the capture");
+        c0->multi_sig.clear();
+        CK(c0, cudaStreamSynchronize(c0->stream));           // a launch in flight may still read the buffer
+        CK(c0, ensure_buf(c0->multi, kMultiHeader + sig.size()));
+        CK(c0, cudaMemcpyAsync(static_cast<char*>(c0->multi.p) + kMultiHeader, sig.data(), sig.size(),
+                               cudaMemcpyHostToDevice, c0->stream));
+        CK(c0, cudaStreamSynchronize(c0->stream));
+        c0->multi_sig = std::move(sig);
+    }
+    char* base = static_cast<char*>(c0->multi.p);
+    out->bar = reinterpret_cast<unsigned*>(base);
+    out->prefix = reinterpret_cast<const long long*>(base + kMultiHeader);
+    out->probs = base + kMultiHeader + pbytes;
+    out->tile = tile;
+    out->max_items = max_items;
+    return PSATD_OK;
+}
+
+template <typename T>
+psatd_status multi_launch(psatd_ctx* const* ctxs, int n, int nsteps, const MultiPrepared& m,
+                          unsigned long long limit_ns, unsigned extra) {
+    psatd_ctx* c0 = ctxs[0];
+    nvtxRangePushA("multi_advance");
+    cudaError_t e = launch_multi_advance<T>(static_cast<const MultiProblem<T>*>(m.probs), m.prefix, n, nsteps, m.tile,
+                                            m.max_items, m.bar, c0->dev_err, limit_ns, extra, c0->stream, nullptr);
+    nvtxRangePop();
+    if (e != cudaSuccess) return cuda_fail(c0, e, "persistent batched advance launch");
+    ++c0->launches;
+    return PSATD_OK;
+}
+
+// Argument checks shared by the batched entry points; errors go to ctxs[0].
+psatd_status multi_check(psatd_ctx* const* ctxs, int n) {
+    if (!ctxs || n < 1) return fail(nullptr, PSATD_ERR_ARG, "need at least one context");
+    for (int p = 0; p < n; ++p)
+        if (!ctxs[p]) return fail(nullptr, PSATD_ERR_ARG, "NULL context in the list");
+    psatd_ctx* c0 = ctxs[0];
+    std::vector<const void*> seen;
+    for (int p = 0; p < n; ++p) {
+        psatd_ctx* c = ctxs[p];
+        psatd_status st = check_ctx(c, true, true);
+        if (st) return fail(c0, st, "context " + std::to_string(p) + ": " + c->err);
+        if (c->real_fields) return fail(c0, PSATD_ERR_STATE, "the batched advance needs complex field storage");
+        if (c->prec != c0->prec) return fail(c0, PSATD_ERR_ARG, "all contexts need the same precision");
+        if (c->stream != c0->stream || c->device != c0->device)
+            return fail(c0, PSATD_ERR_ARG, "all contexts need the same device and stream");
+        for (int a = 0; a < 3; ++a)
+            if (axis_n(c->grid, a) > kMultiMaxN)
+                return fail(c0, PSATD_ERR_SIZE, "the batched advance takes axis lengths up to 1024");
+        seen.push_back(c->fields);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return fail(c0, PSATD_ERR_ARG, "two contexts share field storage");
+    return check_ctx(c0, true, true);
+}
+
 }  // namespace
 
 extern "C" {
@@ -749,6 +943,7 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->lprof);
+    free_buf(c->multi);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
     free_buf(c->samp_g); free_buf(c->samp_h); free_buf(c->samp_out);
     for (auto& p : c->pending) { c->ev_pool.push_back(p.a); c->ev_pool.push_back(p.b); }
@@ -1337,6 +1532,142 @@ const char* psatd_kernel_name(int kind) {
                                                     "init_pulse", "sample_plane", "diagnostics",
                                                     "plane_xy"};
     return (kind >= 0 && kind < PSATD_KERNEL_KINDS) ? names[kind] : "unknown";
+}
+
+psatd_status psatd_multi_advance(psatd_ctx* const* ctxs, int n_ctx, const int* n_steps) {
+    psatd_status st = multi_check(ctxs, n_ctx);
+    if (st) return st;
+    psatd_ctx* c0 = ctxs[0];
+    if (!n_steps) return fail(c0, PSATD_ERR_ARG, "NULL step counts");
+    int nmax = 0;
+    for (int p = 0; p < n_ctx; ++p) {
+        if (n_steps[p] < 0) return fail(c0, PSATD_ERR_ARG, "step counts must be >= 0");
+        nmax = std::max(nmax, n_steps[p]);
+    }
+    if (nmax == 0) return PSATD_OK;
+    MultiPrepared m;
+    if (c0->prec == 64) {
+        if ((st = multi_prepare<double>(ctxs, n_ctx, n_steps, nullptr, nullptr, &m))) return st;
+        if ((st = multi_launch<double>(ctxs, n_ctx, nmax, m, kMultiWaitNs, 0))) return st;
+    } else {
+        if ((st = multi_prepare<float>(ctxs, n_ctx, n_steps, nullptr, nullptr, &m))) return st;
+        if ((st = multi_launch<float>(ctxs, n_ctx, nmax, m, kMultiWaitNs, 0))) return st;
+    }
+    psatd_batch* b = capturing(c0);
+    for (int p = 0; p < n_ctx; ++p) {
+        if (b) b->time_advance.push_back({ctxs[p], n_steps[p] * ctxs[p]->dt});
+        else ctxs[p]->t += n_steps[p] * ctxs[p]->dt;
+    }
+    return PSATD_OK;
+}
+
+psatd_status psatd_multi_autotune(psatd_ctx* const* ctxs, int n_ctx, int trial_steps, double* ms_per_step) {
+    psatd_status st = multi_check(ctxs, n_ctx);
+    if (st) return st;
+    psatd_ctx* c0 = ctxs[0];
+    if (trial_steps < 1) return fail(c0, PSATD_ERR_ARG, "trial_steps must be >= 1");
+    if (capturing(c0)) return fail(c0, PSATD_ERR_STATE, "cannot tune inside a batch capture");
+    // trials run on copies of the fields
+    std::vector<size_t> off((size_t)n_ctx + 1, 0);
+    for (int p = 0; p < n_ctx; ++p) off[p + 1] = off[p] + (6 * n_cells(ctxs[p]->grid) * cplx_size(c0->prec) + 255) / 256 * 256;
+    DevBuf tmp;
+    CK(c0, ensure_buf(tmp, off[n_ctx]));
+    std::vector<void*> fields((size_t)n_ctx);
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < n_ctx && e == cudaSuccess; ++p) {
+        fields[p] = static_cast<char*>(tmp.p) + off[p];
+        e = cudaMemcpyAsync(fields[p], ctxs[p]->fields, 6 * n_cells(ctxs[p]->grid) * cplx_size(c0->prec),
+                            cudaMemcpyDeviceToDevice, c0->stream);
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    const std::vector<int> steps((size_t)n_ctx, trial_steps);
+    std::map<int, MultiChoice> cur;
+    for (int p = 0; p < n_ctx; ++p)
+        for (int a = 0; a < 3; ++a) {
+            const int N = axis_n(ctxs[p]->grid, a);
+            cur[N] = multi_choice(c0->prec, N);
+        }
+    double best_ms = -1.0;
+    auto trial = [&](double* ms) -> psatd_status {
+        MultiPrepared m;
+        psatd_status s2 = c0->prec == 64 ? multi_prepare<double>(ctxs, n_ctx, steps.data(), fields.data(), &cur, &m)
+                                         : multi_prepare<float>(ctxs, n_ctx, steps.data(), fields.data(), &cur, &m);
+        if (s2) return s2;
+        CK(c0, cudaEventRecord(ev[0], c0->stream));
+        s2 = c0->prec == 64 ? multi_launch<double>(ctxs, n_ctx, trial_steps, m, kMultiWaitNs, 0)
+                            : multi_launch<float>(ctxs, n_ctx, trial_steps, m, kMultiWaitNs, 0);
+        if (s2) return s2;
+        CK(c0, cudaEventRecord(ev[1], c0->stream));
+        CK(c0, cudaEventSynchronize(ev[1]));
+        float f = 0.f;
+        CK(c0, cudaEventElapsedTime(&f, ev[0], ev[1]));
+        *ms = f;
+        return check_device_error(c0);
+    };
+    if (e == cudaSuccess) {
+        st = trial(&best_ms);                                  // warm-up (first launch of the kernel)
+        if (st == PSATD_OK) st = trial(&best_ms);
+        // coordinate descent over the axis lengths: each length tries every
+        // distinct radix schedule and tile-width scale with the others fixed
+        for (auto it = cur.begin(); st == PSATD_OK && it != cur.end(); ++it) {
+            const int N = it->first;
+            std::vector<AxisPlan> tried;
+            MultiChoice best = it->second;
+            for (int v = 0; v < kPlanVariants && st == PSATD_OK; ++v) {
+                AxisPlan pl;
+                if (!make_plan_variant(N, v, &pl)) continue;
+                bool dup = false;
+                for (const AxisPlan& q : tried) dup = dup || same_plan(q, pl);
+                if (dup) continue;
+                tried.push_back(pl);
+                for (int sc = -1; sc <= 1 && st == PSATD_OK; ++sc) {
+                    const MultiChoice ch{v, sc};
+                    if (ch == best) continue;
+                    it->second = ch;
+                    double ms = 0.0;
+                    st = trial(&ms);
+                    if (st == PSATD_OK && ms < best_ms) {
+                        best_ms = ms;
+                        best = ch;
+                    }
+                }
+            }
+            it->second = best;
+        }
+    }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    cudaStreamSynchronize(c0->stream);
+    free_buf(tmp);
+    c0->multi_sig.clear();                                     // the uploaded boxes point at the freed copies
+    if (e != cudaSuccess) return cuda_fail(c0, e, "autotune set-up");
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_multi_mutex);
+        for (auto& kv : cur) g_multi_tuned[{c0->prec, kv.first}] = kv.second;
+    }
+    if (ms_per_step) *ms_per_step = best_ms / trial_steps;
+    return PSATD_OK;
+}
+
+psatd_status psatd_selftest_grid_barrier_timeout(psatd_ctx* c) {
+    psatd_ctx* ctxs[1] = {c};
+    psatd_status st = multi_check(ctxs, 1);
+    if (st) return st;
+    if (capturing(c)) return fail(c, PSATD_ERR_STATE, "not allowed while a batch is being captured");
+    MultiPrepared m;
+    const int one = 1;
+    st = c->prec == 64 ? multi_prepare<double>(ctxs, 1, &one, nullptr, nullptr, &m)
+                       : multi_prepare<float>(ctxs, 1, &one, nullptr, nullptr, &m);
+    if (st) return st;
+    // one extra arrival that never comes: every block's first barrier wait
+    // expires after 2 ms
+    st = c->prec == 64 ? multi_launch<double>(ctxs, 1, 1, m, 2000000ull, 1)
+                       : multi_launch<float>(ctxs, 1, 1, m, 2000000ull, 1);
+    if (st) return st;
+    return psatd_synchronize(c);
 }
 
 }  // extern "C"

@@ -15,7 +15,7 @@ namespace psatd {
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 // Device error bits reported through the context's error word.
-enum DeviceError : int { DEV_ERR_TMA_TIMEOUT = 1 };
+enum DeviceError : int { DEV_ERR_TMA_TIMEOUT = 1, DEV_ERR_GRID_TIMEOUT = 2 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

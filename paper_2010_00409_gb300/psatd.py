@@ -34,6 +34,7 @@ EXPORTS = (
     "psatd_fno_create", "psatd_fno_destroy", "psatd_fno_num_params", "psatd_fno_buffers", "psatd_fno_forward",
     "psatd_fno_loss_backward", "psatd_fno_adam_step", "psatd_fno_synchronize", "psatd_fno_last_error",
     "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile", "psatd_fp64_fma_probe",
+    "psatd_multi_advance", "psatd_multi_autotune", "psatd_selftest_grid_barrier_timeout",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -122,6 +123,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_fno_last_error": (C.c_char_p, [P]),
         "psatd_set_mapping": (C.c_int, [P, C.POINTER(PsatdMapping)]),
         "psatd_fp64_fma_probe": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P]),
+        "psatd_multi_advance": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int)]),
+        "psatd_multi_autotune": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.POINTER(C.c_double)]),
+        "psatd_selftest_grid_barrier_timeout": (C.c_int, [P]),
         "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
                                       C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }
@@ -312,6 +316,29 @@ def fp64_fma_probe(out, blocks, threads, iters, stream=None):
     return out
 
 
+def _ctx_array(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c._ptr.value for c in ctxs])
+    return arr
+
+
+def multi_advance(ctxs, n_steps):
+    """Advance the contexts in one persistent launch: n_steps is one count for
+    all or a list with one count per context (the contexts share one stream and
+    precision; errors come from ctxs[0])."""
+    counts = [int(n_steps)] * len(ctxs) if np.isscalar(n_steps) else [int(n) for n in n_steps]
+    assert len(counts) == len(ctxs)
+    arr = (C.c_int * len(ctxs))(*counts)
+    _check(lib().psatd_multi_advance(_ctx_array(ctxs), len(ctxs), arr), ctxs[0]._ptr)
+
+
+def multi_autotune(ctxs, trial_steps: int = 1) -> float:
+    """Tune the batched advance's radix schedules and tile widths per axis
+    length; returns the best time per step in ms."""
+    ms = C.c_double()
+    _check(lib().psatd_multi_autotune(_ctx_array(ctxs), len(ctxs), trial_steps, C.byref(ms)), ctxs[0]._ptr)
+    return ms.value
+
+
 class Context:
     """One periodic box on the current CUDA device; fields are a torch tensor
     [6, Nz, Ny, Nx] (complex64 or complex128, or float32 with real=True) bound
@@ -457,6 +484,10 @@ class Context:
         path, shift, ms = C.c_int(), C.c_int(), C.c_double()
         _check(lib().psatd_autotune(self._ptr, trial_steps, C.byref(path), C.byref(shift), C.byref(ms)), self._ptr)
         return path.value, shift.value, ms.value
+
+    def selftest_grid_barrier_timeout(self) -> int:
+        """Status of the batched advance's barrier self-test (ERR_TIMEOUT expected)."""
+        return lib().psatd_selftest_grid_barrier_timeout(self._ptr)
 
     def set_kernel_path(self, path: int):
         _check(lib().psatd_set_kernel_path(self._ptr, path), self._ptr)

@@ -72,6 +72,13 @@ def test_bad_arguments_rejected_without_device(L):
     assert lib.psatd_fp64_fma_probe(buf, 1, 48, 1, None) == L.ERR_ARG
     assert lib.psatd_fp64_fma_probe(buf, 1, 2048, 1, None) == L.ERR_ARG
     assert lib.psatd_fp64_fma_probe(buf, 1, 32, 0, None) == L.ERR_ARG
+    ctxs = (C.c_void_p * 2)(None, None)
+    ms = C.c_double()
+    steps = (C.c_int * 2)(1, 1)
+    assert lib.psatd_multi_advance(None, 0, steps) == L.ERR_ARG
+    assert lib.psatd_multi_advance(ctxs, 2, steps) == L.ERR_ARG
+    assert lib.psatd_multi_autotune(ctxs, 0, 1, C.byref(ms)) == L.ERR_ARG
+    assert lib.psatd_selftest_grid_barrier_timeout(None) == L.ERR_ARG
 
 
 def test_d_min_host_helper_matches_oracle(L):
