@@ -169,8 +169,9 @@ template <typename T> size_t multi_tile_bytes(int axis, int N_axis, int W);
 // Persistent cooperative launch advancing nprob boxes by up to nsteps PSATD
 // steps (box p by its own probs[p].nsteps <= nsteps).
 // prefix[a][p] (a = 0, 1, 2; p = 0..nprob) are the first work items of box p in
-// the x, y and z phases; tile_bytes the largest tile; bar a device counter the
-// launch resets first; err the device error word; limit_ns the bound of each
+// the x, y and z phases; tile_bytes the largest tile; bar 16 bytes of device
+// memory (8-byte aligned: the barrier and work-ticket counters) the launch
+// resets first; err the device error word; limit_ns the bound of each
 // barrier wait; extra > 0 makes every barrier unreachable (self-test of the
 // bounded wait).  The grid is the co-resident block count (at most max_items).
 template <typename T>

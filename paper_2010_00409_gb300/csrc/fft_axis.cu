@@ -1,9 +1,10 @@
 // Generic in-place FFT along one axis of a [ncomp][Nz][Ny][Nx] complex array
 // (the 3D DFT of Sec. 2.1 is three of these; the kernel is exp(-ikx) forward).
 //
-// Each block stages a tile of W pencils in shared memory (pencil stride P =
-// N + 1, odd, so the strided loads hit distinct banks), runs the Stockham
-// passes between two shared buffers, and writes the pencils back.
+// Each block stages a tile of W pencils in shared memory (the padded pencil
+// layout of fft_core.cuh, odd pencil stride P, so the strided loads hit
+// distinct banks), runs the Stockham passes between two shared buffers, and
+// writes the pencils back.
 //  - x (contiguous): W consecutive rows, loaded and stored as one run.
 //  - y / z (strided): W consecutive x-columns at one (comp, z) or (comp, y),
 //    loaded row by row so each warp touches W*sizeof(complex) contiguous bytes.
@@ -30,15 +31,16 @@ fft_axis_kernel(cplx<T>* __restrict__ data, int axis, int Nx, int Ny, int Nz, in
         const long long row0 = (long long)blockIdx.x * W;
         const int nrow = (int)min((long long)W, rows - row0);
         cplx<T>* base = data + row0 * Nx;
+        const FastDiv dn = fast_div(Nx);
         for (int e = tid; e < nrow * Nx; e += nthr) {
-            const int w = e / Nx, n = e - w * Nx;
-            A[w * P + n] = base[e];
+            const int w = fdiv(e, dn), n = e - w * Nx;
+            A[w * P + pad32(n)] = base[e];
         }
         __syncthreads();
         cplx<T>* res = fft_tile<T, S>(A, B, pl, nrow, P, tw);
         for (int e = tid; e < nrow * Nx; e += nthr) {
-            const int w = e / Nx, n = e - w * Nx;
-            base[e] = res[w * P + n];
+            const int w = fdiv(e, dn), n = e - w * Nx;
+            base[e] = res[w * P + pad32(n)];
         }
         return;
     }
@@ -55,31 +57,33 @@ fft_axis_kernel(cplx<T>* __restrict__ data, int axis, int Nx, int Ny, int Nz, in
     const int nw = min(W, Nx - x0);
     const size_t stride = (axis == 1) ? (size_t)Nx : plane;
     cplx<T>* base = data + (size_t)comp * plane * Nz + (axis == 1 ? (size_t)o * plane : (size_t)o * Nx) + x0;
+    const FastDiv dw = fast_div(nw);
     for (int e = tid; e < N * nw; e += nthr) {
-        const int n = e / nw, w = e - n * nw;
-        A[w * P + n] = base[(size_t)n * stride + w];
+        const int n = fdiv(e, dw), w = e - n * nw;
+        A[w * P + pad32(n)] = base[(size_t)n * stride + w];
     }
     __syncthreads();
     cplx<T>* res = fft_tile<T, S>(A, B, pl, nw, P, tw);
     for (int e = tid; e < N * nw; e += nthr) {
-        const int n = e / nw, w = e - n * nw;
-        base[(size_t)n * stride + w] = res[w * P + n];
+        const int n = fdiv(e, dw), w = e - n * nw;
+        base[(size_t)n * stride + w] = res[w * P + pad32(n)];
     }
 }
 
 // Tile width for an axis: strided axes take up to 128 contiguous bytes per row
 // of the tile; x takes enough rows for ~2048 elements.  Shared memory is
-// capped at 96 KB so two blocks fit on an SM.
+// capped at 56 KB (float32) / 96 KB (float64) so four / two blocks fit on an SM.
 template <typename T>
 void choose_tile(int axis, int N, int Nx, int shift, int* W, int* P) {
     const int es = (int)sizeof(cplx<T>);
-    *P = N + 1;
+    const size_t cap = es == 8 ? 56 * 1024 : 96 * 1024;
+    *P = pencil_stride(N);
     int w;
     if (axis == 0) w = max(1, min(64, 2048 / max(N, 1)));
     else w = min(Nx, 128 / es);
     if (shift > 0) w = min(axis == 0 ? 128 : Nx, w << shift);
     if (shift < 0) w = max(1, w >> -shift);
-    while (w > 1 && 2 * (size_t)w * (*P) * es > 96 * 1024) w /= 2;
+    while (w > 1 && 2 * (size_t)w * (*P) * es > cap) w /= 2;
     *W = max(1, w);
 }
 

@@ -147,25 +147,55 @@ __host__ __device__ __forceinline__ void dft_r(cplx<T>* v) {
     else if constexpr (R == 8) bfly8<T, S>(v);
 }
 
-// One Stockham pass over `W` pencils of length N stored with stride P in
-// `in`, written to `out`.  Work items b = tid, tid + nthr, ... < W*N/R.
-// tw[t] = exp(-2 pi i t / N); the inverse uses its conjugate.
+// Shared-memory layout of a tile of W pencils: element i of pencil w sits at
+// w * P + pad32(i), pad32(i) = i + i / 32.  The one unused slot per 32 elements
+// spreads the stride-R stores of the early Stockham passes (R consecutive
+// outputs per thread) over the banks, and the pencil stride P (odd, at least
+// pad32(N - 1) + 1) keeps the row-by-row tile loads of strided axes on
+// distinct banks.
+__host__ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ int pencil_stride(int N) { return (N + ((N - 1) >> 5)) | 1; }
+
+// Division by a per-pass constant d as a multiply-high: q = umulhi(n, m) with
+// m = ceil(2^32 / d) equals n / d for 0 <= n < 2^16 and 1 <= d < 2^16 (the
+// error term n (m - 2^32/d) / 2^32 < 2^-16 stays below the gap 1/d to the next
+// integer); d = 1 is taken apart.  For d >= 2, ceil(2^32 / d) = (2^32 - 1) / d
+// + 1 (a 32-bit division, once per pass).
+struct FastDiv {
+    unsigned m;
+    int d;
+};
+__host__ __device__ __forceinline__ FastDiv fast_div(int d) {
+    FastDiv f;
+    f.d = d;
+    f.m = d <= 1 ? 0u : 0xFFFFFFFFu / (unsigned)d + 1u;
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+    return f.d <= 1 ? n : (int)__umulhi((unsigned)n, f.m);
+}
+
+// One Stockham pass over `W` pencils of length N (layout above) in `in`,
+// written to `out`.  Work items b = tid, tid + nthr, ... < W*N/R (fewer than
+// 2^16).  tw[t] = exp(-2 pi i t / N); the inverse uses its conjugate.
 template <typename T, int R, int S>
-__host__ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in,
-                                                       cplx<T>* __restrict__ out, int N, int Ns,
-                                                       int W, int P, const cplx<T>* __restrict__ tw,
-                                                       int tid, int nthr) {
+__device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int N,
+                                              int Ns, int W, int P, const cplx<T>* __restrict__ tw, int tid,
+                                              int nthr) {
     const int nb = N / R;
     const int tstride = N / (Ns * R);
+    const FastDiv dnb = fast_div(nb), dns = fast_div(Ns);
     for (int b = tid; b < W * nb; b += nthr) {
-        const int w = b / nb;
+        const int w = fdiv(b, dnb);
         const int j = b - w * nb;
         const cplx<T>* src = in + (size_t)w * P;
         cplx<T>* dst = out + (size_t)w * P;
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
-        const int k = j % Ns;
+        for (int r = 0; r < R; ++r) v[r] = src[pad32(j + r * nb)];
+        const int jq = fdiv(j, dns);
+        const int k = j - jq * Ns;
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -174,16 +204,15 @@ __host__ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict
             }
         }
         dft_r<T, R, S>(v);
-        const int idx = (j / Ns) * Ns * R + k;
+        const int idx = jq * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[idx + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[pad32(idx + r * Ns)] = v[r];
     }
 }
 
 template <typename T, int S>
-__host__ __device__ __forceinline__ void stockham_dispatch(int R, const cplx<T>* in, cplx<T>* out,
-                                                           int N, int Ns, int W, int P,
-                                                           const cplx<T>* tw, int tid, int nthr) {
+__device__ __forceinline__ void stockham_dispatch(int R, const cplx<T>* in, cplx<T>* out, int N, int Ns, int W,
+                                                  int P, const cplx<T>* tw, int tid, int nthr) {
     switch (R) {
         case 2: stockham_pass<T, 2, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
         case 3: stockham_pass<T, 3, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
@@ -192,6 +221,7 @@ __host__ __device__ __forceinline__ void stockham_dispatch(int R, const cplx<T>*
         default: stockham_pass<T, 8, S>(in, out, N, Ns, W, P, tw, tid, nthr); break;
     }
 }
+#endif
 
 #ifdef __CUDACC__
 // Full transform of a shared-memory tile, ping-ponging between a and b.

@@ -77,10 +77,11 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     const size_t comp_tile = (size_t)W * P;
     cplx<T>* base = data + (size_t)y * Nx + x0;
 
+    const FastDiv dw = fast_div(nw), dz = fast_div(Nz);
     for (int c = 0; c < 6; ++c) {
         for (int e = tid; e < Nz * nw; e += nthr) {
-            const int n = e / nw, w = e - n * nw;
-            F[c * comp_tile + w * P + n] = base[c * cstride + (size_t)n * plane + w];
+            const int n = fdiv(e, dw), w = e - n * nw;
+            F[c * comp_tile + w * P + pad32(n)] = base[c * cstride + (size_t)n * plane + w];
         }
     }
     __syncthreads();
@@ -98,12 +99,12 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
     const int ay = min(y, Ny - y);
     for (int e = tid; e < nw * Nz; e += nthr) {
-        const int w = e / Nz, n = e - w * Nz;
+        const int w = fdiv(e, dz), n = e - w * Nz;
         const int ix = x0 + w;
         const int ax = min(ix, Nx - ix), az = min(n, Nz - n);
         const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
         const T nxv = kx[ix] * m.kinv, nyv = ky[y] * m.kinv, nzv = kz[n] * m.kinv;
-        const size_t o = (size_t)w * P + n;
+        const size_t o = (size_t)w * P + pad32(n);
         mode_update<T>(F + o, F + comp_tile + o, F + 2 * comp_tile + o, F + 3 * comp_tile + o,
                        F + 4 * comp_tile + o, F + 5 * comp_tile + o, nxv, nyv, nzv, m.C, m.S, mode,
                        scale);
@@ -122,8 +123,8 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
 
     for (int c = 0; c < 6; ++c) {
         for (int e = tid; e < Nz * nw; e += nthr) {
-            const int n = e / nw, w = e - n * nw;
-            base[c * cstride + (size_t)n * plane + w] = F[c * comp_tile + w * P + n];
+            const int n = fdiv(e, dw), w = e - n * nw;
+            base[c * cstride + (size_t)n * plane + w] = F[c * comp_tile + w * P + pad32(n)];
         }
     }
 }
@@ -170,11 +171,14 @@ template <typename T>
 cudaError_t launch_kspace_z(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, int mode,
                             double scale, cudaStream_t s, long long* nlaunch) {
     const int es = (int)sizeof(cplx<T>);
-    const int P = g.Nz + 1;
-    int W = min(g.Nx, 128 / es);
+    const int P = pencil_stride(g.Nz);
+    // 64 contiguous bytes per tile row; the tile capped at 56 KB (float32, four
+    // blocks per SM) or 100 KB (float64, two)
+    const size_t cap = es == 8 ? 56 * 1024 : 100 * 1024;
+    int W = min(g.Nx, 64 / es);
     if (tb.tile_shift > 0) W = min(g.Nx, W << tb.tile_shift);
     if (tb.tile_shift < 0) W = max(1, W >> -tb.tile_shift);
-    while (W > 1 && 7 * (size_t)W * P * es > 200 * 1024) W /= 2;
+    while (W > 1 && 7 * (size_t)W * P * es > cap) W /= 2;
     const size_t smem = 7 * (size_t)W * P * es;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const long long nblocks = (long long)g.Ny * ((g.Nx + W - 1) / W);

@@ -5,7 +5,8 @@
 // forward and inverse 3D DFTs): x forward, y forward, the fused z pass (z
 // forward, the per-mode update, z inverse), y inverse, x inverse.  Each phase is
 // one list of work items over all boxes (box p owns items [pre[p], pre[p+1])),
-// which the resident blocks take in turn; a grid-wide barrier separates the
+// which the resident blocks draw one at a time from a global ticket counter
+// (a block that drew small items takes more); a grid-wide barrier separates the
 // phases, because a phase reads what every block wrote in the one before.  The
 // launch runs n steps, i.e. 5 n - 1 barriers, without returning to the host;
 // a box with fewer steps of its own skips its items in the later steps.
@@ -79,7 +80,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, unsigned 
 // x phase: rows row0 .. row0 + nrow - 1 of the box ([6][Nz][Ny] rows of Nx).
 template <typename T, int S>
 __device__ void x_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
-    const int Nx = P.N[0], W = P.W[0], Pp = Nx + 1;
+    const int Nx = P.N[0], W = P.W[0], Pp = pencil_stride(Nx);
     const long long rows = 6LL * P.N[1] * P.N[2];
     const long long row0 = item * W;
     const int nrow = (int)min((long long)W, rows - row0);
@@ -87,22 +88,23 @@ __device__ void x_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* B = sm + (size_t)W * Pp;
     cplx<T>* base = P.f + row0 * Nx;
     const int n = nrow * Nx;
+    const FastDiv dn = fast_div(Nx);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int w = e / Nx, i = e - w * Nx;
-        A[w * Pp + i] = __ldcg(base + e);
+        const int w = fdiv(e, dn), i = e - w * Nx;
+        A[w * Pp + pad32(i)] = __ldcg(base + e);
     }
     __syncthreads();
     const cplx<T>* res = fft_tile<T, S>(A, B, P.plan[0], nrow, Pp, P.tw[0]);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int w = e / Nx, i = e - w * Nx;
-        base[e] = res[w * Pp + i];
+        const int w = fdiv(e, dn), i = e - w * Nx;
+        base[e] = res[w * Pp + pad32(i)];
     }
 }
 
 // y phase: x-columns x0 .. x0 + nw - 1 of plane (comp, z).
 template <typename T, int S>
 __device__ void y_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
-    const int Nx = P.N[0], Ny = P.N[1], Nz = P.N[2], W = P.W[1], Pp = Ny + 1;
+    const int Nx = P.N[0], Ny = P.N[1], Nz = P.N[2], W = P.W[1], Pp = pencil_stride(Ny);
     const int ntile = (Nx + W - 1) / W;
     const int t = (int)(item % ntile);
     const long long rest = item / ntile;                      // comp * Nz + z
@@ -113,15 +115,16 @@ __device__ void y_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* B = sm + (size_t)W * Pp;
     cplx<T>* base = P.f + (size_t)comp * plane * Nz + (size_t)z * plane + x0;
     const int n = Ny * nw;
+    const FastDiv dw = fast_div(nw);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int r = e / nw, w = e - r * nw;
-        A[w * Pp + r] = __ldcg(base + (size_t)r * Nx + w);
+        const int r = fdiv(e, dw), w = e - r * nw;
+        A[w * Pp + pad32(r)] = __ldcg(base + (size_t)r * Nx + w);
     }
     __syncthreads();
     const cplx<T>* res = fft_tile<T, S>(A, B, P.plan[1], nw, Pp, P.tw[1]);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int r = e / nw, w = e - r * nw;
-        base[(size_t)r * Nx + w] = res[w * Pp + r];
+        const int r = fdiv(e, dw), w = e - r * nw;
+        base[(size_t)r * Nx + w] = res[w * Pp + pad32(r)];
     }
 }
 
@@ -139,7 +142,7 @@ __device__ void z_transform(cplx<T>* Fc, cplx<T>* scratch, const MultiProblem<T>
 // z phase: x-columns x0 .. x0 + nw - 1 at one y, all six components.
 template <typename T>
 __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
-    const int Nx = P.N[0], Ny = P.N[1], Nz = P.N[2], W = P.W[2], Pp = Nz + 1;
+    const int Nx = P.N[0], Ny = P.N[1], Nz = P.N[2], W = P.W[2], Pp = pencil_stride(Nz);
     const int ntile = (Nx + W - 1) / W;
     const int t = (int)(item % ntile);
     const int y = (int)(item / ntile);
@@ -149,10 +152,11 @@ __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* scratch = sm + 6 * ct;                           // [W][Pp]
     cplx<T>* base = P.f + (size_t)y * Nx + x0;
     const int n = Nz * nw;
+    const FastDiv dw = fast_div(nw), dz = fast_div(Nz);
     for (int c = 0; c < 6; ++c)
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int r = e / nw, w = e - r * nw;
-            F[c * ct + w * Pp + r] = __ldcg(base + c * cstride + (size_t)r * plane + w);
+            const int r = fdiv(e, dw), w = e - r * nw;
+            F[c * ct + w * Pp + pad32(r)] = __ldcg(base + c * cstride + (size_t)r * plane + w);
         }
     __syncthreads();
     for (int c = 0; c < 6; ++c) z_transform<T, -1>(F + c * ct, scratch, P, nw, Pp);
@@ -161,11 +165,11 @@ __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     const int ay = min(y, Ny - y);
     const T ky = P.k[1][y];
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int w = e / Nz, r = e - w * Nz;
+        const int w = fdiv(e, dz), r = e - w * Nz;
         const int ix = x0 + w;
         const int ax = min(ix, Nx - ix), az = min(r, Nz - r);
         const ModeCoef<T> m = P.coef[((size_t)az * Nyh + ay) * Nxh + ax];
-        cplx<T>* o = F + w * Pp + r;
+        cplx<T>* o = F + w * Pp + pad32(r);
         cplx<T> Ex = o[0], Ey = o[ct], Ez = o[2 * ct], Bx = o[3 * ct], By = o[4 * ct], Bz = o[5 * ct];
         rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, P.k[0][ix] * m.kinv, ky * m.kinv, P.k[2][r] * m.kinv, m.C, m.S);
         o[0] = Ex; o[ct] = Ey; o[2 * ct] = Ez;
@@ -176,35 +180,50 @@ __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
 
     for (int c = 0; c < 6; ++c)
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int r = e / nw, w = e - r * nw;
-            base[c * cstride + (size_t)r * plane + w] = F[c * ct + w * Pp + r];
+            const int r = fdiv(e, dw), w = e - r * nw;
+            base[c * cstride + (size_t)r * plane + w] = F[c * ct + w * Pp + pad32(r)];
         }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kMT)
 multi_advance_kernel(const MultiProblem<T>* __restrict__ probs, const long long* __restrict__ prefix, int nprob,
-                     int nsteps, unsigned* bar, int* err, unsigned long long limit_ns, unsigned extra) {
+                     int nsteps, unsigned* bar, unsigned long long* ticket, int* err, unsigned long long limit_ns,
+                     unsigned extra) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MultiProblem<T>* P = reinterpret_cast<MultiProblem<T>*>(smem_raw);
     cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw + desc_bytes<T>());
+    __shared__ long long s_item;
+    int cur = -1;                                               // box whose descriptor is in P
     unsigned nbar = 0;
+    unsigned long long base = 0;                                // first ticket of this phase
     for (int s = 0; s < nsteps; ++s) {
         for (int ph = 0; ph < 5; ++ph) {
             const int a = ph <= 2 ? ph : 4 - ph;               // axis of the phase: x, y, z, y, x
             const long long* pre = prefix + (size_t)a * (nprob + 1);
             const long long total = pre[nprob];
-            for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+            // items are handed out one at a time from a global ticket counter, so
+            // blocks that drew cheap items (small boxes) take more of them; every
+            // block stops at its first ticket past the phase, so the phase uses
+            // exactly total + gridDim.x tickets
+            for (;;) {
+                if (threadIdx.x == 0) s_item = (long long)(atomicAdd(ticket, 1ull) - base);
+                __syncthreads();
+                const long long g = s_item;
+                if (g >= total) break;
                 int lo = 0, hi = nprob - 1;                     // the box p with pre[p] <= g < pre[p + 1]
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (pre[mid] <= g) lo = mid;
                     else hi = mid - 1;
                 }
-                const int* src = reinterpret_cast<const int*>(probs + lo);
-                int* dst = reinterpret_cast<int*>(P);
-                for (int i = threadIdx.x; i < (int)(sizeof(MultiProblem<T>) / 4); i += blockDim.x) dst[i] = src[i];
-                __syncthreads();
+                if (lo != cur) {
+                    const int* src = reinterpret_cast<const int*>(probs + lo);
+                    int* dst = reinterpret_cast<int*>(P);
+                    for (int i = threadIdx.x; i < (int)(sizeof(MultiProblem<T>) / 4); i += blockDim.x) dst[i] = src[i];
+                    cur = lo;
+                    __syncthreads();
+                }
                 const long long item = g - pre[lo];
                 if (s < P->nsteps) {                            // a box past its own step count is skipped
                     if (ph == 0) x_tile<T, -1>(*P, item, tile);
@@ -213,8 +232,9 @@ multi_advance_kernel(const MultiProblem<T>* __restrict__ probs, const long long*
                     else if (ph == 3) y_tile<T, +1>(*P, item, tile);
                     else x_tile<T, +1>(*P, item, tile);
                 }
-                __syncthreads();                                // the next item reuses the descriptor and tile
+                __syncthreads();                                // the next item reuses s_item, the descriptor and tile
             }
+            base += (unsigned long long)total + gridDim.x;
             if (s == nsteps - 1 && ph == 4) return;
             ++nbar;
             if (!grid_barrier(bar, nbar * gridDim.x + extra, err, limit_ns)) return;
@@ -227,7 +247,7 @@ multi_advance_kernel(const MultiProblem<T>* __restrict__ probs, const long long*
 template <typename T>
 size_t multi_tile_bytes(int axis, int N_axis, int W) {
     const size_t es = sizeof(cplx<T>);
-    return (axis == 2 ? 7 : 2) * (size_t)W * (N_axis + 1) * es;
+    return (axis == 2 ? 7 : 2) * (size_t)W * pencil_stride(N_axis) * es;
 }
 
 template <typename T>
@@ -245,7 +265,9 @@ cudaError_t launch_multi_advance(const MultiProblem<T>* probs, const long long* 
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sms;
     if (max_items < grid) grid = max_items < 1 ? 1 : max_items;
-    if ((e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    // barrier counter at bar[0], ticket counter at bar[2] (8-byte aligned)
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(bar + 2);
+    if ((e = cudaMemsetAsync(bar, 0, 16, s)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
     cfg.blockDim = dim3(kMT, 1, 1);
@@ -257,7 +279,7 @@ cudaError_t launch_multi_advance(const MultiProblem<T>* probs, const long long* 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (grid_out) *grid_out = (int)grid;
-    return cudaLaunchKernelEx(&cfg, k, probs, prefix, nprob, nsteps, bar, err, limit_ns, extra);
+    return cudaLaunchKernelEx(&cfg, k, probs, prefix, nprob, nsteps, bar, ticket, err, limit_ns, extra);
 }
 
 template size_t multi_tile_bytes<float>(int, int, int);
