@@ -5,8 +5,10 @@ CPU legs of bench.py; never by the product path.
 
 Everything here is float64 numpy, written from the paper (arXiv:2010.00409,
 "Tight focusing of short pulses by mapping to periodic space"), each function
-citing the section / equation it follows.  Library primitives used as single
-steps: ``numpy.fft.fftn`` / ``ifftn`` (the 3D DFT) and matrix products.
+citing the section / equation it follows.  The 3D DFT is this module's own
+recursive decimation-in-time transform (one split near sqrt(N) per level,
+direct sums of length <= 32 at the leaves), pinned against the brute-force
+sum; library primitives used as single steps: matrix products.
 
 Field layout: ``fields[6, Nz, Ny, Nx]`` complex128, components
 (Ex, Ey, Ez, Bx, By, Bz), x fastest.  Node (i, j, l) sits at
@@ -131,18 +133,66 @@ class Pulse:
 # Spectral solver (Sec. 2.1)
 # ----------------------------------------------------------------------------
 def wavenumbers(N: int, d: float) -> np.ndarray:
-    """k_m = 2*pi*m/(N*d), m in fftfreq order (R2)."""
-    return 2.0 * np.pi * np.fft.fftfreq(N, d)
+    """k_m = 2*pi*m/(N*d) with m = i for i < (N+1)/2 and m = i - N above (R2:
+    the even-N Nyquist index is -N/2)."""
+    i = np.arange(N)
+    m = np.where(i < (N + 1) // 2, i, i - N)
+    return 2.0 * np.pi * m / (N * d)
+
+
+def _split(N: int) -> int:
+    """Factor p split off at one level of the recursive DFT: the largest divisor
+    of N not above sqrt(N); 1 (sum directly) for N <= 32 or N prime."""
+    if N <= 32:
+        return 1
+    for p in range(int(math.isqrt(N)), 1, -1):
+        if N % p == 0:
+            return p
+    return 1
+
+
+def _unit_roots(e: np.ndarray, N: int, sign: int) -> np.ndarray:
+    """exp(sign*2*pi*i*e/N) for integer exponents e, reduced modulo N first."""
+    return np.exp(sign * 2j * np.pi * (np.mod(e, N) / N))
+
+
+def _dft_last(x: np.ndarray, sign: int) -> np.ndarray:
+    """DFT along the last axis, X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N), by
+    decimation in time.  With N = p*M, n = p*m + r and k = k1 + M*k2:
+        X[k1 + M*k2] = sum_r exp(sign*2*pi*i*r*k2/p) exp(sign*2*pi*i*r*k1/N) Y_r[k1],
+    Y_r the M-point DFT of the subsequence x[r::p] (computed by recursion).
+    Short or prime lengths are summed directly (a product with the DFT
+    matrix)."""
+    N = x.shape[-1]
+    p = _split(N)
+    if p == 1:
+        n = np.arange(N)
+        return x @ _unit_roots(np.outer(n, n), N, sign)
+    M = N // p
+    r, k1 = np.arange(p), np.arange(M)
+    xr = x.reshape(x.shape[:-1] + (M, p))                       # xr[..., m, r] = x[p*m + r]
+    Y = _dft_last(np.swapaxes(xr, -1, -2), sign)                 # Y[..., r, k1]
+    Y = np.swapaxes(Y, -1, -2) * _unit_roots(np.outer(k1, r), N, sign)   # twiddled, [..., k1, r]
+    Z = Y @ _unit_roots(np.outer(r, r), p, sign)                 # Z[..., k1, k2]
+    return np.swapaxes(Z, -1, -2).reshape(x.shape)               # k = k1 + M*k2
+
+
+def _dft3(f: np.ndarray, sign: int) -> np.ndarray:
+    out = np.asarray(f, dtype=np.complex128)
+    for axis in (-1, -2, -3):
+        out = np.moveaxis(_dft_last(np.moveaxis(out, axis, -1), sign), -1, axis)
+    return out
 
 
 def fft3(f: np.ndarray) -> np.ndarray:
     """Unnormalised forward 3D DFT over the last three axes, kernel exp(-i k.x) (R1)."""
-    return np.fft.fftn(f, axes=(-3, -2, -1))
+    return _dft3(f, -1)
 
 
 def ifft3(F: np.ndarray) -> np.ndarray:
     """Inverse 3D DFT with the 1/(Nx*Ny*Nz) factor (R1)."""
-    return np.fft.ifftn(F, axes=(-3, -2, -1))
+    N = F.shape[-1] * F.shape[-2] * F.shape[-3]
+    return _dft3(F, +1) / N
 
 
 def _dft_matrix(N: int, sign: int) -> np.ndarray:

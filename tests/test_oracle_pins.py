@@ -25,7 +25,10 @@ def small_grid(Nx=8, Ny=6, Nz=10, c=1.0):
 
 
 # --------------------------------------------------------------------------- FFT
-@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 6, 6), (10, 6, 8), (6, 10, 12), (1, 3, 5)])
+# lengths above 32 take the recursive split (64 = 8 x 8, 40 = 5 x 8, 35 = 5 x 7,
+# 96 = 8 x 12 then 12 directly); 37 is prime and summed directly
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 6, 6), (10, 6, 8), (6, 10, 12), (1, 3, 5),
+                                   (2, 3, 64), (1, 40, 3), (35, 2, 1), (1, 1, 96), (1, 2, 37)])
 def test_fft3_equals_bruteforce_sum(shape):
     f = W.random_complex_field((2,) + shape, seed=1)
     F = O.fft3(f)
@@ -34,6 +37,24 @@ def test_fft3_equals_bruteforce_sum(shape):
     back = O.ifft3(F)
     assert np.max(np.abs(back - f)) <= 1e-14 * np.max(np.abs(f)) * 10
     assert np.max(np.abs(O.idft3_naive(Fb) - f)) <= 1e-12 * np.max(np.abs(f))
+
+
+def test_fft3_split_catches_a_planted_twiddle_mistake(monkeypatch):
+    """A twiddle of the split with the wrong index (r*k2 instead of r*k1) is
+    caught by the brute-force comparison."""
+    good = O._unit_roots
+    calls = {"n": 0}
+
+    def bad(e, N, sign):
+        calls["n"] += 1
+        return good(e.T if e.shape[0] != e.shape[1] else e + 1, N, sign)
+
+    f = W.random_complex_field((1, 1, 2, 64), seed=4)
+    Fb = O.dft3_naive(f, -1)
+    monkeypatch.setattr(O, "_unit_roots", bad)
+    F = O.fft3(f)
+    assert calls["n"] > 0
+    assert np.max(np.abs(F - Fb)) > 1e-3 * np.max(np.abs(Fb))
 
 
 def test_fft_sign_convention_puts_plane_wave_at_plus_m():
