@@ -76,6 +76,9 @@ def args_parse():
                     help="PSATD steps of the 1024^3 multi-octave run (0: to the focus, then the stepped "
                          "focal field is compared with float64 too)")
     ap.add_argument("--storage", choices=("real", "complex"), default="real")
+    ap.add_argument("--jsonl", default=os.environ.get("PSATD_METRICS_LOG"),
+                    help="append a condensed record of the run to this JSON-lines file "
+                         "(default: $PSATD_METRICS_LOG, else none)")
     a = ap.parse_args()
     if a.storage == "real" and not real_storage_supported(a.size):
         a.storage = "complex"          # the real-field kernels cover 256 x 256 x {64, 128, 256}
@@ -224,6 +227,9 @@ def run_reference(a):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    if a.jsonl:
+        from paper_2010_00409_gb300 import metrics
+        metrics.append(a.jsonl, metrics.bench_record(line))
 
 
 def workload_config(size, storage="real"):
@@ -350,6 +356,9 @@ def run_ours(a):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if a.jsonl:
+            from paper_2010_00409_gb300 import metrics
+            metrics.append(a.jsonl, metrics.bench_record(line))
 
 
 def multi_octave_measure(dev, stream, k=8):
@@ -614,11 +623,22 @@ def fp64_peak_measure(dev, stream, iters=4096, reps=5):
     return 16.0 * iters * blocks * threads / (ms * 1e-3) / 1e12
 
 
+# Executed float64 instructions per cell-step of the 256^3 float64 step (ncu
+# sass counters over its five launches: x, y, the fused z pass, y, x), from the
+# capture summarised in profiles/fp64_step_256.md; re-take when those kernels
+# change.  DADD + DMUL + DFMA thread instructions, and their flops (DFMA = 2).
+FP64_EXECUTED_256 = {"instr_per_cell_step": 900.56, "flop_per_cell_step": 1078.84,
+                     "fp64_pipe_active_pct": "84.7-86.7", "source": "profiles/fp64_step_256.md"}
+
+
 def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
     """The plain float64 GPU solver on the same grid: n PSATD steps, with its
-    arithmetic roofline: nominal flops per cell-step (5 N log2 N per complex
-    transform of N points, forward and inverse, six components, plus 80 for the
-    per-mode update) against the float64 FMA rate measured by the probe."""
+    arithmetic roofline.  The float64 pipe issues one DADD, DMUL or DFMA per lane
+    per cycle, so the bound is the instruction rate: executed float64
+    instructions per cell-step (ncu, FP64_EXECUTED_256) against the probe's rate
+    (its flops / 2: DFMA chains).  The nominal-flop figure (5 N log2 N per
+    complex transform, forward and inverse, six components, plus 80 for the
+    update) is kept beside it."""
     import torch
     from paper_2010_00409_gb300 import psatd
     peak = fp64_peak_measure(dev, stream)
@@ -636,12 +656,27 @@ def fp64_measure(g, m, p, n_steps, dt, dev, stream, n=10):
         ms = e0.elapsed_time(e1)
         prof = c.profile_read()
     flop = 2 * 6 * 5 * math.log2(g.cells) + 80
-    achieved = flop * g.cells * n / (ms * 1e-3) / 1e12
-    return {"value": g.cells * n / (ms / 1e3), "unit": UNIT, "psatd_steps": n, "ms_per_psatd_step": ms / n,
-            "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "flop_per_cell_step": flop,
-                         "peak_source": "measured in this run: float64 FMA chains (psatd_fp64_fma_probe)"}}
+    rate = g.cells * n / (ms * 1e-3)
+    achieved = flop * rate / 1e12
+    res = {"value": rate, "unit": UNIT, "psatd_steps": n, "ms_per_psatd_step": ms / n,
+           "kernel_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()},
+           "nominal_flop_roofline": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak, "flop_per_cell_step": flop}}
+    if g.Nx == 256 and g.Ny == 256 and g.Nz == 256:
+        ex = FP64_EXECUTED_256
+        instr = ex["instr_per_cell_step"] * rate / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": instr, "peak": peak / 2, "unit": "T fp64 instr/s",
+                           "frac": instr / (peak / 2), "instr_per_cell_step": ex["instr_per_cell_step"],
+                           "executed_flop_per_cell_step": ex["flop_per_cell_step"],
+                           "executed_TFLOPs": ex["flop_per_cell_step"] * rate / 1e12,
+                           "fp64_pipe_active_pct_ncu": ex["fp64_pipe_active_pct"], "counters_from": ex["source"],
+                           "peak_source": "measured in this run: float64 FMA chains (psatd_fp64_fma_probe), "
+                                          "instructions = flops / 2"}
+    else:
+        res["roofline"] = dict(res["nominal_flop_roofline"], bound="alu",
+                               note="executed-instruction counters were taken at 256^3 only")
+    res["roofline"].setdefault("peak_source", "measured in this run: float64 FMA chains (psatd_fp64_fma_probe)")
+    return res
 
 
 def focal_forms(ctx32, g, m, p, n_steps, plane, dt, dev, stream, stepped32, ms_step64, reps=5):

@@ -273,6 +273,22 @@ psatd_status psatd_selftest_wait_timeout(psatd_ctx* ctx);
 psatd_status psatd_energy_noalloc(const void* fields, int precision, long long n_cells, double* out,
                                   int out_on_device, void* cuda_stream);
 
+/* Failure injection for host-side tests (the paper has no counterpart).
+ * psatd_debug_set_alloc_limit caps the bytes of device memory the library's
+ * contexts hold (fields it allocates, tables, scratch): an allocation that
+ * would pass the cap fails as cudaMalloc would (the call returns
+ * PSATD_ERR_OOM) without reaching the driver; bytes < 0 removes the cap.
+ * psatd_debug_alloc_live returns the bytes held now.
+ * psatd_debug_inject_cuda_error makes the after_calls-th checked CUDA call of
+ * the C ABI from now (counted over all contexts; a step launch of
+ * psatd_advance counts as one) return cuda_error (a cudaError_t value) without
+ * being made, so the entry point returns PSATD_ERR_CUDA (PSATD_ERR_OOM for
+ * cudaErrorMemoryAllocation); after_calls <= 0 disarms.  Both are
+ * process-wide and not synchronised with calls in flight on other threads. */
+void psatd_debug_set_alloc_limit(long long bytes);
+long long psatd_debug_alloc_live(void);
+void psatd_debug_inject_cuda_error(int after_calls, int cuda_error);
+
 /* Batches: record a sequence of calls on contexts that share one (non-default)
  * CUDA stream into a CUDA graph and replay it with a single launch, e.g. one
  * exact step per pulse realisation for parameter sweeps.  Between

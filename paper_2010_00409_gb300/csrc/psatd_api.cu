@@ -12,6 +12,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -154,10 +155,56 @@ psatd_status cuda_fail(psatd_ctx* c, cudaError_t e, const char* where) {
     return fail(c, e == cudaErrorMemoryAllocation ? PSATD_ERR_OOM : PSATD_ERR_CUDA, m);
 }
 
-#define CK(ctx, call)                                                   \
-    do {                                                                \
-        cudaError_t e_ = (call);                                        \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+// ---------------------------------------------------------------------------
+// Failure injection for host-side tests (psatd_debug_*): a cap on the bytes of
+// device memory the library holds (an allocation past it fails as cudaMalloc
+// would, without calling it), and an armed CUDA error that replaces the result
+// of the n-th checked call from now (the call itself is skipped).
+std::mutex g_alloc_mutex;
+std::map<void*, size_t> g_alloc_sizes;
+long long g_alloc_live = 0;
+long long g_alloc_limit = -1;                     // -1: no cap
+std::atomic<int> g_inject_after{0};               // 0: nothing armed
+std::atomic<int> g_inject_error{0};
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_alloc_limit >= 0 && g_alloc_live + (long long)bytes > g_alloc_limit) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        g_alloc_sizes[*p] = bytes;
+        g_alloc_live += (long long)bytes;
+    }
+    return e;
+}
+
+void lib_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    auto it = g_alloc_sizes.find(p);
+    if (it != g_alloc_sizes.end()) {
+        g_alloc_live -= (long long)it->second;
+        g_alloc_sizes.erase(it);
+    }
+}
+
+// True (once) when the armed error is due at this checked call.
+bool inject_due() {
+    int n = g_inject_after.load();
+    while (n > 0) {
+        if (g_inject_after.compare_exchange_weak(n, n - 1)) return n == 1;
+    }
+    return false;
+}
+
+#define CK(ctx, call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = inject_due() ? (cudaError_t)g_inject_error.load() : (call);         \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);                           \
     } while (0)
 
 size_t cplx_size(int prec) { return prec == 64 ? 16 : 8; }
@@ -166,7 +213,7 @@ size_t n_cells(const psatd_grid& g) { return (size_t)g.Nx * g.Ny * g.Nz; }
 size_t value_size(const psatd_ctx* c) { return c->real_fields ? sizeof(float) : cplx_size(c->prec); }
 
 void free_buf(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) lib_free(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -174,7 +221,7 @@ void free_buf(DevBuf& b) {
 cudaError_t ensure_buf(DevBuf& b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return cudaSuccess;
     free_buf(b);
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = lib_malloc(&b.p, bytes);
     if (e == cudaSuccess) b.bytes = bytes;
     else b.p = nullptr;
     return e;
@@ -902,13 +949,13 @@ psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mappin
     if (st == PSATD_OK) st = set_coef(c, dt);
     if (st == PSATD_OK && real) st = upload_slot_tables(c);
     if (st == PSATD_OK) {
-        e = cudaMalloc(&c->dev_err, sizeof(int));
+        e = lib_malloc(reinterpret_cast<void**>(&c->dev_err), sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(error word)");
     }
     if (st == PSATD_OK && !(flags & PSATD_FLAG_NO_FIELD_ALLOC)) {
         const size_t bytes = 6 * n_cells(*grid) * value_size(c);
-        e = cudaMalloc(&c->fields, bytes);
+        e = lib_malloc(&c->fields, bytes);
         if (e != cudaSuccess) {
             c->fields = nullptr;
             st = cuda_fail(c, e, "cudaMalloc(fields)");
@@ -934,8 +981,8 @@ void psatd_destroy(psatd_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    if (c->own_fields && c->fields) cudaFree(c->fields);
-    if (c->dev_err) cudaFree(c->dev_err);
+    if (c->own_fields && c->fields) lib_free(c->fields);
+    if (c->dev_err) lib_free(c->dev_err);
     for (int a = 0; a < 3; ++a) { free_buf(c->tw[a]); free_buf(c->k[a]); }
     free_buf(c->coef);
     free_buf(c->coef_T);
@@ -1001,7 +1048,7 @@ psatd_status psatd_bind_fields(psatd_ctx* c, void* dev_ptr, size_t bytes) {
         return fail(c, PSATD_ERR_ARG, "field storage must be device memory");
     if (c->own_fields && c->fields) {
         CK(c, cudaStreamSynchronize(c->stream));
-        cudaFree(c->fields);
+        lib_free(c->fields);
     }
     c->fields = dev_ptr;
     c->field_bytes = bytes;
@@ -1127,7 +1174,8 @@ psatd_status psatd_advance(psatd_ctx* c, int n_steps) {
     psatd_batch* b = capturing(c);
     if (b && c->prof_on) return fail(c, PSATD_ERR_STATE, "profiling must be off while capturing a batch");
     for (int s = 0; s < n_steps; ++s) {
-        cudaError_t e = c->real_fields ? spectral_pass_real(c)
+        cudaError_t e = inject_due() ? (cudaError_t)g_inject_error.load()
+                        : c->real_fields ? spectral_pass_real(c)
                         : c->prec == 64 ? spectral_pass<double>(c, KS_ROTATE, 0.0)
                                         : spectral_pass<float>(c, KS_ROTATE, 0.0);
         if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
@@ -1446,7 +1494,7 @@ psatd_status psatd_autotune(psatd_ctx* c, int trial_steps, int* path_out, int* s
     }
     // trial runs on a scratch copy so the context's fields stay untouched
     void* scratch = nullptr;
-    CK(c, cudaMalloc(&scratch, c->field_bytes));
+    CK(c, lib_malloc(&scratch, c->field_bytes));
     void* saved = c->fields;
     const double t_saved = c->t;
     const bool prof_saved = c->prof_on;
@@ -1486,7 +1534,7 @@ psatd_status psatd_autotune(psatd_ctx* c, int trial_steps, int* path_out, int* s
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(c->stream);
-    cudaFree(scratch);
+    lib_free(scratch);
     if (err != cudaSuccess) return cuda_fail(c, err, "autotune trial");
     c->kernel_path = best_path;
     c->tile_shift = best_shift;
@@ -1668,6 +1716,21 @@ psatd_status psatd_selftest_grid_barrier_timeout(psatd_ctx* c) {
                        : multi_launch<float>(ctxs, 1, 1, m, 2000000ull, 1);
     if (st) return st;
     return psatd_synchronize(c);
+}
+
+void psatd_debug_set_alloc_limit(long long bytes) {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_alloc_limit = bytes < 0 ? -1 : bytes;
+}
+
+long long psatd_debug_alloc_live(void) {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    return g_alloc_live;
+}
+
+void psatd_debug_inject_cuda_error(int after_calls, int cuda_error) {
+    g_inject_error.store(cuda_error);
+    g_inject_after.store(after_calls > 0 ? after_calls : 0);
 }
 
 }  // extern "C"

@@ -35,6 +35,7 @@ EXPORTS = (
     "psatd_fno_loss_backward", "psatd_fno_adam_step", "psatd_fno_synchronize", "psatd_fno_last_error",
     "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile", "psatd_fp64_fma_probe",
     "psatd_multi_advance", "psatd_multi_autotune", "psatd_selftest_grid_barrier_timeout",
+    "psatd_debug_set_alloc_limit", "psatd_debug_alloc_live", "psatd_debug_inject_cuda_error",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -126,6 +127,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_multi_advance": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int)]),
         "psatd_multi_autotune": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.POINTER(C.c_double)]),
         "psatd_selftest_grid_barrier_timeout": (C.c_int, [P]),
+        "psatd_debug_set_alloc_limit": (None, [C.c_longlong]),
+        "psatd_debug_alloc_live": (C.c_longlong, []),
+        "psatd_debug_inject_cuda_error": (None, [C.c_int, C.c_int]),
         "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
                                       C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }

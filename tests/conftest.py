@@ -20,3 +20,16 @@ def lib():
         pytest.skip("no CUDA device")
     from paper_2010_00409_gb300 import psatd
     return psatd
+
+
+@pytest.fixture
+def metrics_log():
+    """log(case, precision, rel_l2, tol): appends a parity record to the file
+    named by $PSATD_METRICS_LOG (nothing when it is unset)."""
+    from paper_2010_00409_gb300 import metrics
+    path = os.environ.get(metrics.ENV)
+
+    def log(case, precision, rel_l2, tol, **extra):
+        if path:
+            metrics.append(path, metrics.parity_record(case, precision, float(rel_l2), tol, **extra))
+    return log
