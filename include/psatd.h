@@ -113,11 +113,15 @@ typedef struct psatd_diag {
  * Nx = Ny = 256 and Nz one of 64, 128, 256 (else PSATD_ERR_ARG).  A real-field
  * step is the real part of the complex step (Sec. 2.1, Eq. 3-4; on Nyquist
  * planes this is the mean of the update at the two mirrored wave vectors) and
- * moves half the bytes.  In that mode psatd_fft and psatd_focal_one_shot
- * return PSATD_ERR_STATE (psatd_energy_noalloc reads complex storage only),
- * psatd_autotune keeps the one real-field kernel set; psatd_init_pulse,
- * psatd_sample_focal_plane and psatd_diagnostics work through a complex scratch
- * copy that the context allocates on first use (48 bytes per cell).
+ * moves half the bytes.  In that mode psatd_fft returns PSATD_ERR_STATE
+ * (psatd_energy_noalloc reads complex storage only) and psatd_autotune keeps
+ * the one real-field kernel set.  psatd_init_pulse writes the (real) pulse
+ * straight into the real storage and projects it with one real-field pass;
+ * psatd_sample_focal_plane reads the real field, and psatd_focal_one_shot
+ * leaves and samples the half spectrum (k_x >= 0, in the slot order of the
+ * real-field plane pass, the x Nyquist modes in a context-owned array; the
+ * negative k_x are their conjugates).  Only psatd_diagnostics works through a
+ * complex scratch copy, allocated on its first use (48 bytes per cell).
  * Cites: Sec. 2.1 (solver), Sec. 2.3 (periodic layer). */
 psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mapping,
                              double dt, int precision, void* cuda_stream, int flags,
@@ -206,7 +210,9 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* ctx, double x_phys, int ny, int
  * or all six components are set again (psatd_sample_focal_plane keeps working,
  * from the spectrum); psatd_time() is T.  The coefficient
  * table for T is built on the host (float64) and cached for the next call with
- * the same T. */
+ * the same T.  With real field storage the spectrum is the half spectrum of
+ * real fields (the update is the real-field one, with the projection of B
+ * folded in) and the sample is the same interpolant of the real field. */
 psatd_status psatd_focal_one_shot(psatd_ctx* ctx, const psatd_pulse* pulse, double T, double x_phys,
                                   int ny, int nz, double y0, double y1, double z0, double z1,
                                   int comp_mask, void* dst, int dst_on_device);

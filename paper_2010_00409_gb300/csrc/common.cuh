@@ -215,6 +215,7 @@ template <typename T> struct HalfSlots {
     const ModeCoef<T>* coef;
     cplx<T>* nyq;
     const CUtensorMap* map_nyq;
+    bool project_e = false;     // project E (mean on Nyquist planes) before the update
 };
 
 // Tensor-copy-fed k-space pass; `map` describes the field as a 4D tensor of
@@ -268,6 +269,10 @@ cudaError_t launch_init_pulse(cplx<T>* data, const GridGeom& g, const ShellGeom&
                               long long* nlaunch);
 
 // Focal-plane sampling scratch and launch.
+// The same pulse written as real float32 values (real field storage).
+cudaError_t launch_init_pulse_real(float* data, const GridGeom& g, const ShellGeom& sh, const PulseParams& p,
+                                   int m_lo, int m_hi, cudaStream_t s, long long* nlaunch);
+
 struct SampleScratch {
     double2* wx;     // [Nx]
     double2* wy;     // [ny][Ny]
@@ -283,6 +288,15 @@ cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const Sh
                                 long long* nlaunch, bool from_spectrum = false);
 
 // Diagnostics: energy partials and spectral divergence partials.
+// Sampling of real float32 storage: from the real field (from_spectrum false),
+// or from the half spectrum the one-shot leaves (slots [6][Nz][Ny][Nx/2] with
+// x mode slot_mode[p], the x Nyquist spectrum in nyq [6][Nz][Ny]).
+cudaError_t launch_sample_plane_real(const float* data, const float2* nyq, const int* slot_mode, const GridGeom& g,
+                                     const ShellGeom& sh, double x_phys, int ny, int nz, double y0, double y1,
+                                     double z0, double z1, double t, const int* comps, int ncomp,
+                                     const SampleScratch& sc, float2* out, cudaStream_t s, long long* nlaunch,
+                                     bool from_spectrum);
+
 template <typename T>
 cudaError_t launch_energy(const cplx<T>* data, size_t n_per_comp, double* partial, int nblocks,
                           cudaStream_t s, long long* nlaunch);

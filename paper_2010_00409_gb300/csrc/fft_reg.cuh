@@ -329,6 +329,22 @@ __device__ __forceinline__ void rotate_mode(cplx<T>& Ex, cplx<T>& Ey, cplx<T>& E
     Ex = nEx; Ey = nEy; Ez = nEz;
 }
 
+// Real fields: the transverse projection of B that keeps the field real, on a
+// Nyquist plane the mean of the projections along n and along m (n with its
+// Nyquist components negated): B <- B - (n(n.B) + m(m.B))/2; off the Nyquist
+// planes m = n and this is B - n(n.B).
+template <typename T>
+__device__ __forceinline__ void project_b_mean(cplx<T>& Bx, cplx<T>& By, cplx<T>& Bz, T nx, T ny, T nz, bool fx,
+                                               bool fy, bool fz) {
+    const T mx = fx ? -nx : nx, my = fy ? -ny : ny, mz = fz ? -nz : nz;
+    const T nBr = nx * Bx.x + ny * By.x + nz * Bz.x, nBi = nx * Bx.y + ny * By.y + nz * Bz.y;
+    const T mBr = mx * Bx.x + my * By.x + mz * Bz.x, mBi = mx * Bx.y + my * By.y + mz * Bz.y;
+    const T h = T(0.5);
+    Bx = mk<T>(Bx.x - h * (nx * nBr + mx * mBr), Bx.y - h * (nx * nBi + mx * mBi));
+    By = mk<T>(By.x - h * (ny * nBr + my * mBr), By.y - h * (ny * nBi + my * mBi));
+    Bz = mk<T>(Bz.x - h * (nz * nBr + mz * mBr), Bz.y - h * (nz * nBi + mz * mBi));
+}
+
 // Real fields: on a Nyquist plane the wave number -pi/d is its own mirror, so the
 // update that keeps the field real is the mean of the update at n and at m = n
 // with the Nyquist components (flags fx, fy, fz) negated:

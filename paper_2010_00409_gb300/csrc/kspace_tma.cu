@@ -56,16 +56,20 @@ __device__ __forceinline__ void group_sync(int h) {
 // comes from kxs and the coefficient table is in slot order along x (column =
 // slot, so neighbouring threads read neighbouring entries; column Nx/2 = the x
 // Nyquist mode), and modes on Nyquist planes take the mean update that keeps the
-// field real.  The x Nyquist spectrum lives in its own array nyq[q][z][k_y]; the
-// blocks after the Ny * Nx/(2W) field tiles take its tiles of W k_y values
-// (copied through map_nyq, a 3D map {Ny, Nz, 6}).
+// field real (project_b / project_e: B / E is first projected the same way, the
+// mean of the projections along the two mirrored wave vectors; that mean is not
+// idempotent on Nyquist planes, so a projection followed by a step needs both).  The x Nyquist spectrum
+// lives in its own array nyq[q][z][k_y]; the blocks after the Ny * Nx/(2W)
+// field tiles take its tiles of W k_y values (copied through map_nyq, a 3D map
+// {Ny, Nz, 6}).  SPECTRAL_OUT with HALF leaves the updated half spectrum (slots
+// and the Nyquist array) in natural k_z order.
 template <typename T, int N1, int N2, int W, int G, bool SPECTRAL_OUT, bool HALF>
 __global__ void __launch_bounds__(W * N2 * G)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_nyq,
                   cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __restrict__ tw,
                   const T* __restrict__ kxs, const T* __restrict__ kys, const T* __restrict__ kzs,
                   const ModeCoef<T>* __restrict__ coef, int* __restrict__ err, bool project_b, int coef_nx,
-                  cplx<T>* __restrict__ nyq, T kx_nyq) {
+                  cplx<T>* __restrict__ nyq, T kx_nyq, bool project_e) {
     constexpr int Nz = N1 * N2;
     constexpr int RP = N2 * W;
     constexpr int SLOT = N1 * RP;
@@ -221,6 +225,10 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
         const ModeCoef<T> mm = mc[m];
         if constexpr (HALF) {
             const bool fz = ((j + N2 * (r / N2)) + N1 * (r % N2)) == Nz / 2;
+            if (project_e)
+                project_b_mean<T>(Ex, Ey, Ez, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
+            if (project_b)
+                project_b_mean<T>(Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
             rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq,
                                 2 * y == Ny, fz, mm.C, mm.S);
         } else {
@@ -311,7 +319,8 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
                               int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     constexpr int G = 2;
     const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
-    auto k = half ? kspace_tma_kernel<T, N1, N2, W, G, false, true>
+    auto k = half ? (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, true>
+                                  : kspace_tma_kernel<T, N1, N2, W, G, false, true>)
                   : (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, false>
                                   : kspace_tma_kernel<T, N1, N2, W, G, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -331,7 +340,7 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
     return cudaLaunchKernelEx(&cfg, k, map, half ? *half->map_nyq : map, data, nx, g.Ny, tb.tw[2],
                               half ? half->k : tb.k[0], tb.k[1], tb.k[2], half ? half->coef : tb.coef, err, project_b,
                               g.Nx / 2 + 1, half ? half->nyq : (cplx<T>*)nullptr,
-                              (T)(-3.14159265358979323846 / g.dx));
+                              (T)(-3.14159265358979323846 / g.dx), half ? half->project_e : false);
 }
 
 // Self-test of the bounded-wait path: waits on an mbarrier whose 16 expected
@@ -363,8 +372,7 @@ template <typename T>
 cudaError_t launch_kspace_tma(const CUtensorMap& map, cplx<T>* data, const GridGeom& g, const Tables<T>& tb,
                               int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     constexpr int W = kspace_tma_width<T>();
-    if ((half ? g.Nx / 2 : g.Nx) % W != 0 || (half && (spectral_out || project_b || g.Ny % W != 0)))
-        return cudaErrorNotSupported;
+    if ((half ? g.Nx / 2 : g.Nx) % W != 0 || (half && g.Ny % W != 0)) return cudaErrorNotSupported;
     switch (g.Nz) {
         case 64: return kspace_tma_launch<T, 8, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);
         case 128: return kspace_tma_launch<T, 16, 8, W>(map, data, g, tb, err, s, spectral_out, project_b, half);

@@ -90,6 +90,8 @@ struct psatd_ctx {
     bool real_fields = false;           // real float32 storage (PSATD_FLAG_REAL_FIELDS)
     DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
     DevBuf slot_k, slot_coef;           // real fields: k_x per slot, coefficient table in slot order
+    DevBuf slot_mode;                   // real fields: x mode index per slot (sampling from the half spectrum)
+    DevBuf slot_coef_proj;              // real fields: projection table (C = 1/Ntot, S = 0) in slot order
     DevBuf nyq;                         // real fields: x Nyquist spectrum [6][Nz][Ny] between the plane kernels
     CUtensorMap nyq_map;                // ... and its tensor map for the k-space kernel (128-B aligned type)
     bool nyq_map_ok = false;
@@ -580,7 +582,13 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
 
 // One real-field step: r2c plane transforms, the half-spectrum k-space pass
 // (field slots and the x Nyquist array in one launch), c2r plane transforms.
-cudaError_t spectral_pass_real(psatd_ctx* c) {
+// coef replaces the step's slot-ordered table (the projection, one step of T);
+// project_b / project_e project B / E before the update (the one-time
+// projection alone: B only, the update projects E; the projection followed by
+// a step: both); spectral_out stops after the k-space pass, leaving the updated
+// half spectrum in natural k_z order.
+cudaError_t spectral_pass_real(psatd_ctx* c, const ModeCoef<float>* coef = nullptr, bool project_b = false,
+                               bool spectral_out = false, bool project_e = false) {
     const GridGeom g = geom(c);
     const Tables<float> tb = tables<float>(c);
     float* f = static_cast<float*>(c->fields);
@@ -592,13 +600,14 @@ cudaError_t spectral_pass_real(psatd_ctx* c) {
     });
     if (e != cudaSuccess) return e;
     const HalfSlots<float> hs{static_cast<const float*>(c->slot_k.p),
-                              static_cast<const ModeCoef<float>*>(c->slot_coef.p), nyq, &c->nyq_map};
+                              coef ? coef : static_cast<const ModeCoef<float>*>(c->slot_coef.p), nyq, &c->nyq_map,
+                              project_e};
     e = timed(c, PSATD_KERNEL_KSPACE, [&] {
         ++c->launches;
         return launch_kspace_tma<float>(c->field_map, reinterpret_cast<cplx<float>*>(f), g, tb, c->dev_err, c->stream,
-                                        false, false, &hs);
+                                        spectral_out, project_b, &hs);
     });
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || spectral_out) return e;
     return timed(c, PSATD_KERNEL_PLANE_XY, [&] {
         ++c->launches;
         return launch_plane_rc(f, nyq, 6, g, tb, +1, c->stream);
@@ -641,6 +650,10 @@ psatd_status upload_slot_tables(psatd_ctx* c) {
         k[p] = (float)(kTwoPi * (double)plane_rc_slot_mode(p) / (c->grid.Nx * c->grid.dx));
     CK(c, ensure_buf(c->slot_k, nh * sizeof(float)));
     CK(c, cudaMemcpy(c->slot_k.p, k.data(), nh * sizeof(float), cudaMemcpyHostToDevice));
+    std::vector<int> mode(nh);
+    for (int p = 0; p < nh; ++p) mode[p] = plane_rc_slot_mode(p);
+    CK(c, ensure_buf(c->slot_mode, nh * sizeof(int)));
+    CK(c, cudaMemcpy(c->slot_mode.p, mode.data(), nh * sizeof(int), cudaMemcpyHostToDevice));
     const size_t nn = (size_t)6 * c->grid.Ny * c->grid.Nz;
     CK(c, ensure_buf(c->nyq, nn * sizeof(float2)));
     CK(c, cudaMemset(c->nyq.p, 0, nn * sizeof(float2)));
@@ -988,6 +1001,7 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef_T);
     free_buf(c->coef_proj);
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
+    free_buf(c->slot_mode); free_buf(c->slot_coef_proj);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->lprof);
     free_buf(c->multi);
@@ -1095,20 +1109,6 @@ psatd_status psatd_get_field(psatd_ctx* c, int comp, void* dst, int dst_on_devic
 psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
-    if (c->real_fields) {
-        // the complex pulse (and projection) in the scratch copy, then its real part
-        st = ensure_scratch(c, false);
-        if (st) return st;
-        {
-            ComplexView v(c);
-            st = psatd_init_pulse(c, p);
-        }
-        if (st) return st;
-        CK(c, launch_narrow(static_cast<const float2*>(c->cscratch.p), static_cast<float*>(c->fields),
-                            6 * n_cells(c->grid), c->stream));
-        ++c->launches;
-        return PSATD_OK;
-    }
     if (!p) return fail(c, PSATD_ERR_ARG, "NULL pulse");
     if (p->kind != PSATD_PULSE_FLAT_TOP && p->kind != PSATD_PULSE_GAUSSIAN && p->kind != PSATD_PULSE_PROFILE)
         return fail(c, PSATD_ERR_ARG, "unknown pulse kind");
@@ -1150,13 +1150,24 @@ psatd_status psatd_init_pulse(psatd_ctx* c, const psatd_pulse* p) {
     ShellGeom sh{c->mapping.R0, c->mapping.L};
     const GridGeom g = geom(c);
     cudaError_t e = timed(c, PSATD_KERNEL_INIT, [&] {
+        if (c->real_fields)                            // the pulse is real: written straight into real storage
+            return launch_init_pulse_real(static_cast<float*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches);
         return c->prec == 64
             ? launch_init_pulse<double>(static_cast<cplx<double>*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches)
             : launch_init_pulse<float>(static_cast<cplx<float>*>(c->fields), g, sh, pp, m_lo, m_hi, c->stream, &c->launches);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init_pulse launch");
     c->holds_spectrum = false;
-    if (p->div_project) {
+    if (p->div_project && c->real_fields) {
+        // the projection as one real-field pass with C = 1/Ntot, S = 0 and B projected
+        if (!c->slot_coef_proj.p) {
+            if (capturing(c)) return fail(c, PSATD_ERR_STATE, "the first projection cannot run inside a batch capture");
+            st = upload_coef<float>(c, 0.0, &c->slot_coef_proj, true, true);
+            if (st) return st;
+        }
+        e = spectral_pass_real(c, static_cast<const ModeCoef<float>*>(c->slot_coef_proj.p), true, false);
+        if (e != cudaSuccess) return cuda_fail(c, e, "projection launch");
+    } else if (p->div_project) {
         const double scale = 1.0 / (double)n_cells(c->grid);
         e = c->prec == 64 ? spectral_pass<double>(c, KS_PROJECT, scale) : spectral_pass<float>(c, KS_PROJECT, scale);
         if (e != cudaSuccess) return cuda_fail(c, e, "projection launch");
@@ -1201,13 +1212,6 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
                                       double z0, double z1, int comp_mask, void* dst, int dst_on_device) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
-    if (c->real_fields) {
-        if (capturing(c)) return fail(c, PSATD_ERR_STATE, "sample_focal_plane is not captured into batches");
-        st = ensure_scratch(c, true);
-        if (st) return st;
-        ComplexView v(c);
-        return psatd_sample_focal_plane(c, x_phys, ny, nz, y0, y1, z0, z1, comp_mask, dst, dst_on_device);
-    }
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
     if (!(is_finite(x_phys) && is_finite(y0) && is_finite(y1) && is_finite(z0) && is_finite(z1)))
@@ -1235,6 +1239,8 @@ psatd_status psatd_sample_focal_plane(psatd_ctx* c, double x_phys, int ny, int n
     ShellGeom sh{c->mapping.R0, c->mapping.L};
     const GridGeom gg = geom(c);
     cudaError_t e = timed(c, PSATD_KERNEL_SAMPLE, [&] {
+        if (c->real_fields)
+            return launch_sample_plane_real(static_cast<const float*>(c->fields), static_cast<const float2*>(c->nyq.p), static_cast<const int*>(c->slot_mode.p), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<float2*>(out), c->stream, &c->launches, c->holds_spectrum);
         return c->prec == 64
             ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches, c->holds_spectrum)
             : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, c->t, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches, c->holds_spectrum);
@@ -1253,7 +1259,6 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
                                   int dst_on_device) {
     psatd_status st = check_ctx(c, true);
     if (st) return st;
-    if (c->real_fields) return fail(c, PSATD_ERR_STATE, "the one-shot path works on complex field storage only");
     if (!is_finite(T)) return fail(c, PSATD_ERR_ARG, "T must be finite");
     if (!dst) return fail(c, PSATD_ERR_ARG, "NULL dst");
     if (ny < 1 || nz < 1 || ny > 4096 || nz > 4096) return fail(c, PSATD_ERR_ARG, "ny, nz must be 1..4096");
@@ -1275,7 +1280,9 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
                                             "dst) must have run once before, with profiling off");
     }
     if (!c->coef_T_ok || c->coef_T_step != T) {
-        st = c->prec == 64 ? upload_coef<double>(c, T, &c->coef_T) : upload_coef<float>(c, T, &c->coef_T);
+        // real fields: the table in the slot order of the half spectrum
+        st = c->prec == 64 ? upload_coef<double>(c, T, &c->coef_T)
+                           : upload_coef<float>(c, T, &c->coef_T, c->real_fields);
         if (st) return st;
         c->coef_T_ok = true;
         c->coef_T_step = T;
@@ -1285,7 +1292,10 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
     p.div_project = 0;
     st = psatd_init_pulse(c, &p);
     if (st) return st;
-    cudaError_t e = c->prec == 64 ? one_shot_spectrum<double>(c, project != 0) : one_shot_spectrum<float>(c, project != 0);
+    cudaError_t e = c->real_fields ? spectral_pass_real(c, static_cast<const ModeCoef<float>*>(c->coef_T.p),
+                                                        project != 0, true, project != 0)
+                    : c->prec == 64 ? one_shot_spectrum<double>(c, project != 0)
+                                    : one_shot_spectrum<float>(c, project != 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "one-shot launch");
     c->holds_spectrum = true;
     c->t = T;
@@ -1311,6 +1321,8 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
     ShellGeom sh{c->mapping.R0, c->mapping.L};
     const GridGeom gg = geom(c);
     e = timed(c, PSATD_KERNEL_SAMPLE, [&] {
+        if (c->real_fields)
+            return launch_sample_plane_real(static_cast<const float*>(c->fields), static_cast<const float2*>(c->nyq.p), static_cast<const int*>(c->slot_mode.p), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, T, comps, nc, sc, static_cast<float2*>(out), c->stream, &c->launches, true);
         return c->prec == 64
             ? launch_sample_plane<double>(static_cast<const cplx<double>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, T, comps, nc, sc, static_cast<cplx<double>*>(out), c->stream, &c->launches, true)
             : launch_sample_plane<float>(static_cast<const cplx<float>*>(c->fields), gg, sh, x_phys, ny, nz, y0, y1, z0, z1, T, comps, nc, sc, static_cast<cplx<float>*>(out), c->stream, &c->launches, true);

@@ -141,8 +141,15 @@ __device__ __forceinline__ void pol_vectors_f(float X, float Y, float Z, float d
     s1[0] = a0 * i1; s1[1] = a1 * i1; s1[2] = a2 * i1;
 }
 
-template <typename T>
-__global__ void init_pulse_kernel(cplx<T>* __restrict__ data, GridGeom g, ShellGeom sh, PulseParams p,
+// One field value: complex storage takes (v, 0), real float32 storage v.
+template <typename T, bool REAL>
+__device__ __forceinline__ void store_value(void* data, size_t i, T v) {
+    if constexpr (REAL) static_cast<float*>(data)[i] = (float)v;
+    else static_cast<cplx<T>*>(data)[i] = mk<T>(v, (T)0);
+}
+
+template <typename T, bool REAL>
+__global__ void init_pulse_kernel(void* __restrict__ data, GridGeom g, ShellGeom sh, PulseParams p,
                                   int m_lo, int m_hi) {
     const size_t n_cells = (size_t)g.Nx * g.Ny * g.Nz;
     const double D = g.Nx * g.dx;
@@ -177,8 +184,8 @@ __global__ void init_pulse_kernel(cplx<T>* __restrict__ data, GridGeom g, ShellG
                 }
             }
             for (int a = 0; a < 3; ++a) {
-                data[a * n_cells + idx] = mk<T>((T)E[a], (T)0);
-                data[(3 + a) * n_cells + idx] = mk<T>((T)B[a], (T)0);
+                store_value<T, REAL>(data, a * n_cells + idx, (T)E[a]);
+                store_value<T, REAL>(data, (3 + a) * n_cells + idx, (T)B[a]);
             }
             continue;
         }
@@ -201,8 +208,8 @@ __global__ void init_pulse_kernel(cplx<T>* __restrict__ data, GridGeom g, ShellG
             }
         }
         for (int a = 0; a < 3; ++a) {
-            data[a * n_cells + idx] = mk<T>((T)E[a], (T)0);
-            data[(3 + a) * n_cells + idx] = mk<T>((T)B[a], (T)0);
+            store_value<T, REAL>(data, a * n_cells + idx, (T)E[a]);
+            store_value<T, REAL>(data, (3 + a) * n_cells + idx, (T)B[a]);
         }
     }
 }
@@ -217,7 +224,18 @@ cudaError_t launch_init_pulse(cplx<T>* data, const GridGeom& g, const ShellGeom&
     const int threads = 256;
     long long blocks = (long long)((n_cells + threads - 1) / threads);
     if (blocks > 152LL * 64) blocks = 152LL * 64;
-    init_pulse_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(data, g, sh, p, m_lo, m_hi);
+    init_pulse_kernel<T, false><<<(unsigned)blocks, threads, 0, s>>>(data, g, sh, p, m_lo, m_hi);
+    if (nlaunch) ++*nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_pulse_real(float* data, const GridGeom& g, const ShellGeom& sh, const PulseParams& p,
+                                   int m_lo, int m_hi, cudaStream_t s, long long* nlaunch) {
+    const size_t n_cells = (size_t)g.Nx * g.Ny * g.Nz;
+    const int threads = 256;
+    long long blocks = (long long)((n_cells + threads - 1) / threads);
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    init_pulse_kernel<float, true><<<(unsigned)blocks, threads, 0, s>>>(data, g, sh, p, m_lo, m_hi);
     if (nlaunch) ++*nlaunch;
     return cudaGetLastError();
 }

@@ -119,6 +119,81 @@ __global__ void contract_x_kernel(const cplx<T>* __restrict__ f, GridGeom g, Com
     if (lane == 0) out[warp] = make_double2(re, im);
 }
 
+// Real float32 fields: g[a][l][j] = sum_i wx[i] f[c_a][l][j][i] with real f.
+__global__ void contract_x_real_kernel(const float* __restrict__ f, GridGeom g, CompList cl, int ncomp,
+                                       const double2* __restrict__ wx, double2* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long rows = (long long)ncomp * g.Nz * g.Ny;
+    if (warp >= rows) return;
+    const int a = (int)(warp / ((long long)g.Nz * g.Ny));
+    const long long rl = warp - (long long)a * g.Nz * g.Ny;
+    const float* row = f + (size_t)cl.c[a] * g.Nx * g.Ny * g.Nz + (size_t)rl * g.Nx;
+    double re = 0.0, im = 0.0;
+    for (int i = lane; i < g.Nx; i += 32) {
+        const double v = (double)row[i];
+        const double2 w = wx[i];
+        re += w.x * v;
+        im += w.y * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) out[warp] = make_double2(re, im);
+}
+
+// Half spectrum of real fields (slots p < Nx/2 holding x mode mode[p], the x
+// Nyquist mode in Q), with the 1/N of the inverse DFT folded in.  The modes with
+// negative k_x are the conjugates F(-k) = conj F(k) of the stored ones, so
+//   g[a][l][j] = A[l][j] + conj(A'[-l][-j]),
+//   A  = sum_p S[p] wx[mode[p]] + Q wx[Nx/2]   (k_x >= 0 and the Nyquist mode),
+//   A' = A without the k_x = 0 and Nyquist terms  (their mirrors are themselves),
+// using conj(F) wx[-k_x] = conj(F wx[k_x]); -l, -j are the mirrored indices
+// (N - l) mod N.  One warp per (a, l, j).
+__global__ void contract_x_half_kernel(const float2* __restrict__ S, const float2* __restrict__ Q, GridGeom g,
+                                       CompList cl, int ncomp, const int* __restrict__ mode,
+                                       const double2* __restrict__ wx, double2* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long rows = (long long)ncomp * g.Nz * g.Ny;
+    if (warp >= rows) return;
+    const int a = (int)(warp / ((long long)g.Nz * g.Ny));
+    const long long rl = warp - (long long)a * g.Nz * g.Ny;
+    const int l = (int)(rl / g.Ny), j = (int)(rl - (long long)l * g.Ny);
+    const int lm = (g.Nz - l) % g.Nz, jm = (g.Ny - j) % g.Ny;
+    const int nh = g.Nx / 2;
+    const size_t cbase = (size_t)cl.c[a] * g.Nz * g.Ny;
+    const float2* row = S + (cbase + (size_t)l * g.Ny + j) * nh;
+    const float2* rowm = S + (cbase + (size_t)lm * g.Ny + jm) * nh;
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+    for (int p = lane; p < nh; p += 32) {
+        const int m = mode[p];
+        const double2 w = wx[m];
+        const float2 v = row[p];
+        ar += w.x * v.x - w.y * v.y;
+        ai += w.x * v.y + w.y * v.x;
+        if (m != 0) {
+            const float2 u = rowm[p];
+            br += w.x * u.x - w.y * u.y;
+            bi += w.x * u.y + w.y * u.x;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, o);
+        ai += __shfl_down_sync(0xffffffffu, ai, o);
+        br += __shfl_down_sync(0xffffffffu, br, o);
+        bi += __shfl_down_sync(0xffffffffu, bi, o);
+    }
+    if (lane == 0) {
+        const double2 w = wx[nh];
+        const float2 q = Q[cbase + (size_t)l * g.Ny + j];
+        ar += w.x * q.x - w.y * q.y;
+        ai += w.x * q.y + w.y * q.x;
+        out[warp] = make_double2(ar + br, ai - bi);
+    }
+}
+
 // h[a][l][p] = sum_j wy[p][j] g[a][l][j]
 __global__ void contract_y_kernel(const double2* __restrict__ gin, GridGeom g, int ncomp, int ny,
                                   const double2* __restrict__ wy, double2* __restrict__ h) {
@@ -185,6 +260,34 @@ cudaError_t launch_sample_plane(const cplx<T>* data, const GridGeom& g, const Sh
     const long long no = (long long)ncomp * nz * ny;
     contract_z_kernel<T><<<(unsigned)((no + 255) / 256), 256, 0, s>>>(sc.h, g, sh, ncomp, ny, nz, x_phys,
                                                                       y0, y1, z0, z1, t, sc.wz, out);
+    if (nlaunch) *nlaunch += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_plane_real(const float* data, const float2* nyq, const int* slot_mode, const GridGeom& g,
+                                     const ShellGeom& sh, double x_phys, int ny, int nz, double y0, double y1,
+                                     double z0, double z1, double t, const int* comps, int ncomp,
+                                     const SampleScratch& sc, float2* out, cudaStream_t s, long long* nlaunch,
+                                     bool from_spectrum) {
+    CompList cl;
+    for (int a = 0; a < 6; ++a) cl.c[a] = a < ncomp ? comps[a] : 0;
+    const int nw = g.Nx + ny * g.Ny + nz * g.Nz;
+    if (from_spectrum)
+        spectral_weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
+    else
+        weights_kernel<<<(nw + 255) / 256, 256, 0, s>>>(g, x_phys, ny, nz, y0, y1, z0, z1, sc.wx, sc.wy, sc.wz);
+    const long long rows = (long long)ncomp * g.Nz * g.Ny;
+    const unsigned xb = (unsigned)((rows * 32 + 255) / 256);
+    if (from_spectrum)
+        contract_x_half_kernel<<<xb, 256, 0, s>>>(reinterpret_cast<const float2*>(data), nyq, g, cl, ncomp, slot_mode,
+                                                  sc.wx, sc.g);
+    else
+        contract_x_real_kernel<<<xb, 256, 0, s>>>(data, g, cl, ncomp, sc.wx, sc.g);
+    const long long nh = (long long)ncomp * g.Nz * ny;
+    contract_y_kernel<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(sc.g, g, ncomp, ny, sc.wy, sc.h);
+    const long long no = (long long)ncomp * nz * ny;
+    contract_z_kernel<float><<<(unsigned)((no + 255) / 256), 256, 0, s>>>(sc.h, g, sh, ncomp, ny, nz, x_phys,
+                                                                          y0, y1, z0, z1, t, sc.wz, out);
     if (nlaunch) *nlaunch += 4;
     return cudaGetLastError();
 }

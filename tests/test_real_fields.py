@@ -102,8 +102,48 @@ def test_real_fields_argument_and_state_errors(lib):
         with pytest.raises(lib.PsatdError):
             ctx.fft(lib.FORWARD)
         p = W.PulseSpec(kind=W.GAUSSIAN, lam=1.0, theta=0.4, eps=0.1, P0=1.0, n_cycles=2.0)
+        ctx.focal_one_shot(p, 1.0, 0.0, 4, 4, -1, 1, -1, 1)
         with pytest.raises(lib.PsatdError):
-            ctx.focal_one_shot(p, 1.0, 0.0, 4, 4, -1, 1, -1, 1)
+            ctx.advance(1)                          # the storage holds the half spectrum now
+        ctx.set_fields(np.zeros((6, 64, 256, 256), np.float32))
         assert ctx.autotune()[0] == lib.PATH_AUTO
         ctx.advance(0)
         assert np.all(ctx.get_field(0) == 0)
+
+
+def _flat_top_layer():
+    lam, R0, L = 1.0, 16.0, 2.0
+    g = W.GridSpec(256, 256, 64, 7.0 / 256, 30.0 / 256, 30.0 / 64, -(R0 - L / 2) - 7.0, -15.0, -15.0, 1.0)
+    return g, W.MappingSpec(R0, L), lam
+
+
+@pytest.mark.parametrize("project", [1, 0])
+def test_real_one_shot_matches_oracle_without_complex_scratch(lib, project):
+    """One exact step of T on real storage (the half spectrum, the real-field
+    update with the projection of B folded in), sampled from that spectrum,
+    against the oracle's real-field exact step and sampling; no complex copy of
+    the field is allocated on the way."""
+    g, m, lam = _flat_top_layer()
+    p = W.PulseSpec(kind=W.FLAT_TOP, lam=lam, theta=np.arctan(1 / 0.6), eps=0.1, P0=1.0, div_project=project)
+    og, om = ogrid(g), O.Mapping(m.R0, m.L)
+    op = O.Pulse(p.kind, p.lam, p.theta, p.eps, p.P0, p.n_cycles, p.cep, p.ellipticity, p.pol_angle, project)
+    f0 = O.init_fields(og, om, op)
+    if project:
+        f0 = O.project_transverse(f0, og)
+    f0 = f0.real
+    T = 9.0
+    ys, zs = np.linspace(-1.5, 1.5, 24, endpoint=False), np.linspace(-1.2, 1.2, 20, endpoint=False)
+    args = (-6.5, 24, 20, -1.5, 1.5, -1.2, 1.2)
+    L = lib.lib()
+    with lib.Context(g, m, T / 10, 32, real=True) as ctx:
+        live0 = L.psatd_debug_alloc_live()
+        got = ctx.focal_one_shot(p, T, *args, comps=(0, 1, 2, 4))
+        grown = L.psatd_debug_alloc_live() - live0
+        assert grown < 6 * g.cells * 8 // 4               # far below a complex copy (48 B per cell)
+        assert abs(ctx.time - T) == 0.0
+        again = ctx.sample_focal_plane(*args, comps=(0, 1, 2, 4))
+        assert np.array_equal(again, got)                  # sampled from the held half spectrum
+    f1 = O.psatd_step_real(f0, og, T)
+    ref = O.sample_plane(f1.astype(np.complex128), og, om, args[0], ys, zs, T, comps=(0, 1, 2, 4))
+    assert np.max(np.abs(ref)) > 1e-2 * np.max(np.abs(f0))
+    assert rel(got, ref) <= 1e-5
