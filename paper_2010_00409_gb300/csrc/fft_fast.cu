@@ -28,10 +28,14 @@ template <typename T, int N1, int N2> struct RowsCfg {
 };
 
 // columns per block for the strided kernel: 128 contiguous bytes per row of the
-// tile, halved until the exchange buffer fits 48 KB of static shared memory
-template <typename T, int N> constexpr int cols_width() {
+// tile, halved until the exchange buffer fits the shared-memory budget: 48 KB
+// along y (rows one plane row apart), 128 KB along z, whose rows lie a whole
+// plane apart (at 1024^2 planes, 32-byte runs 8 MB apart used the DRAM bursts
+// poorly: the z transforms took 2.3 times as long as with 128-byte runs)
+template <typename T, int N, bool ZAXIS> constexpr int cols_width() {
+    const int budget = ZAXIS ? 128 * 1024 : 48 * 1024;
     int w = 128 / (int)sizeof(cplx<T>);
-    while (w > 1 && N * w * (int)sizeof(cplx<T>) > 48 * 1024) w /= 2;
+    while (w > 1 && N * w * (int)sizeof(cplx<T>) > budget) w /= 2;
     return w;
 }
 
@@ -86,7 +90,8 @@ template <typename T, int N1, int N2, int W, int S>
 __global__ void __launch_bounds__(W * N2)
 fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, const cplx<T>* __restrict__ tw) {
     constexpr int RS = N2 * W, ES = W;
-    __shared__ cplx<T> scratch[N1 * N2 * W];
+    extern __shared__ __align__(16) unsigned char cols_smem[];
+    cplx<T>* scratch = reinterpret_cast<cplx<T>*>(cols_smem);     // [N1 * N2 * W]
     const int c = threadIdx.x % W, j = threadIdx.x / W;
     const size_t plane = (size_t)Nx * Ny;
     const int ntile = Nx / W;
@@ -211,6 +216,21 @@ kspace_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __
     }
 }
 
+template <typename T, int N1, int N2, int W>
+cudaError_t cols_launch(cplx<T>* data, int ncomp, const GridGeom& g, const cplx<T>* tw, int axis, int dir,
+                        cudaStream_t s) {
+    if (g.Nx % W != 0) return cudaErrorNotSupported;
+    const long long blocks = (long long)ncomp * (axis == 1 ? g.Nz : g.Ny) * (g.Nx / W);
+    const size_t smem = (size_t)N1 * N2 * W * sizeof(cplx<T>);
+    auto k = dir < 0 ? fft_cols_kernel<T, N1, N2, W, -1> : fft_cols_kernel<T, N1, N2, W, +1>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, W * N2, smem, s>>>(data, g.Nx, g.Ny, g.Nz, axis, tw);
+    return cudaGetLastError();
+}
+
 template <typename T, int N1, int N2>
 cudaError_t axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, const cplx<T>* tw, int axis, int dir,
                       cudaStream_t s) {
@@ -223,13 +243,8 @@ cudaError_t axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, const cplx<T>
         else fft_rows_kernel<T, N1, N2, +1><<<blocks, Cfg::threads, 0, s>>>(data, rows, tw);
         return cudaGetLastError();
     }
-    constexpr int W = cols_width<T, N>();
-    if (g.Nx % W != 0) return cudaErrorNotSupported;
-    const long long blocks = (long long)ncomp * (axis == 1 ? g.Nz : g.Ny) * (g.Nx / W);
-    (void)N;
-    if (dir < 0) fft_cols_kernel<T, N1, N2, W, -1><<<(unsigned)blocks, W * N2, 0, s>>>(data, g.Nx, g.Ny, g.Nz, axis, tw);
-    else fft_cols_kernel<T, N1, N2, W, +1><<<(unsigned)blocks, W * N2, 0, s>>>(data, g.Nx, g.Ny, g.Nz, axis, tw);
-    return cudaGetLastError();
+    return axis == 2 ? cols_launch<T, N1, N2, cols_width<T, N, true>()>(data, ncomp, g, tw, axis, dir, s)
+                     : cols_launch<T, N1, N2, cols_width<T, N, false>()>(data, ncomp, g, tw, axis, dir, s);
 }
 
 }  // namespace
