@@ -292,6 +292,14 @@ psatd_status psatd_energy_noalloc(const void* fields, int precision, long long n
  * cudaErrorMemoryAllocation); after_calls <= 0 disarms.  Both are
  * process-wide and not synchronised with calls in flight on other threads. */
 void psatd_debug_set_alloc_limit(long long bytes);
+/* In a library built with -DPSATD_DEBUG (libpsatd_debug.so) every global index
+ * of the field, table and scratch buffers the kernels touch is checked against
+ * its buffer: an index outside the buffer is counted and replaced by 0 (the
+ * access stays inside), the first one kept with its bound.  This call
+ * synchronises the device, returns the number of such indices since the last
+ * call (and clears it) and writes the first index and bound when it is > 0;
+ * -1 on a CUDA error, -2 in a library built without the checks. */
+long long psatd_debug_bounds_report(long long* first_index, long long* first_bound);
 long long psatd_debug_alloc_live(void);
 void psatd_debug_inject_cuda_error(int after_calls, int cuda_error);
 

@@ -50,8 +50,8 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -59,29 +59,39 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build_library(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile csrc/*.cu and link libpsatd.so; skipped when sources are unchanged."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_file = os.path.join(BUILD, "stamp")
+DEBUG_LIB = os.path.join(HERE, "libpsatd_debug.so")
+
+
+def build_library(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile csrc/*.cu and link libpsatd.so; skipped when sources are unchanged.
+
+    debug=True builds libpsatd_debug.so with -DPSATD_DEBUG: every instrumented
+    global index is bounds-checked (psatd_debug_bounds_report)."""
+    lib = DEBUG_LIB if debug else LIB
+    bdir = BUILD + ("_debug" if debug else "")
+    extra = tuple(extra) + (("-DPSATD_DEBUG",) if debug else ())
+    os.makedirs(bdir, exist_ok=True)
+    stamp_file = os.path.join(bdir, "stamp")
     stamp = _stamp() + repr(tuple(extra))
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         if open(stamp_file).read() == stamp:
-            return LIB
+            return lib
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
+    LIB_ = lib
+    tmp = LIB_ + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, LIB_)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
     if verbose:
-        print("built", LIB, file=sys.stderr)
-    return LIB
+        print("built", LIB_, file=sys.stderr)
+    return LIB_
 
 
 if __name__ == "__main__":
-    build_library(force="--force" in sys.argv, verbose=True)
+    build_library(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv)

@@ -9,6 +9,60 @@
 namespace psatd {
 
 // ---------------------------------------------------------------------------
+// Bounds-checked global indices (builds with -DPSATD_DEBUG).  PSATD_IX(i, n) is
+// the index i of a global buffer of n elements.  In a debug build an index
+// outside [0, n) is counted (the first one is kept with its bound) and replaced
+// by 0, so the access stays inside the buffer; psatd_debug_bounds_report reads
+// and clears the counts of every translation unit.  In other builds it is i.
+#ifdef PSATD_DEBUG
+void debug_register_reader(long long (*reader)(long long* first_index, long long* first_bound));
+namespace dbg {
+static __device__ unsigned long long g_oob;
+static __device__ long long g_first[2];
+__device__ __forceinline__ long long idx(long long i, long long n) {
+    if (i < 0 || i >= n) {
+        if (atomicAdd(&g_oob, 1ull) == 0ull) {
+            g_first[0] = i;
+            g_first[1] = n;
+        }
+        return 0;
+    }
+    return i;
+}
+// this translation unit's counts, read and cleared (host)
+static long long read_and_clear(long long* first_index, long long* first_bound) {
+    unsigned long long n = 0;
+    long long f[2] = {0, 0};
+    if (cudaMemcpyFromSymbol(&n, g_oob, sizeof n) != cudaSuccess) return -1;
+    cudaMemcpyFromSymbol(f, g_first, sizeof f);
+    const unsigned long long zero = 0;
+    cudaMemcpyToSymbol(g_oob, &zero, sizeof zero);
+    if (first_index) *first_index = f[0];
+    if (first_bound) *first_bound = f[1];
+    return (long long)n;
+}
+struct Registrar {
+    Registrar() { debug_register_reader(&read_and_clear); }
+};
+static Registrar g_registrar;
+}  // namespace dbg
+#define PSATD_IX(i, n) (::psatd::dbg::idx((long long)(i), (long long)(n)))
+#else
+#define PSATD_IX(i, n) (i)
+#endif
+
+// A global buffer of n elements: at(p, k) is p[k] for a pointer p into it,
+// bounds-checked against the whole buffer in debug builds.
+template <typename V> struct GBuf {
+    V* base;
+    long long n;
+    __device__ __forceinline__ V& at(const V* p, long long k) const {
+        return base[PSATD_IX((long long)(p - base) + k, n)];
+    }
+    __device__ __forceinline__ V& operator[](long long i) const { return base[PSATD_IX(i, n)]; }
+};
+
+// ---------------------------------------------------------------------------
 // complex helpers over float2 / double2
 // ---------------------------------------------------------------------------
 template <typename T> struct vec2;

@@ -44,12 +44,14 @@ energy_kernel(const cplx<T>* __restrict__ f, size_t n, double* __restrict__ part
     __shared__ double sh[kThreads / 32];
     double eE = 0.0, eB = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        eE += cell_energy3<T>(f[i], f[n + i], f[2 * n + i]);
-        eB += cell_energy3<T>(f[3 * n + i], f[4 * n + i], f[5 * n + i]);
+        const GBuf<const cplx<T>> F{f, 6LL * (long long)n};
+        eE += cell_energy3<T>(F[i], F[n + i], F[2 * n + i]);
+        eB += cell_energy3<T>(F[3 * n + i], F[4 * n + i], F[5 * n + i]);
     }
     const double sE = block_sum(eE, sh);
     const double sB = block_sum(eB, sh);
-    if (threadIdx.x == 0) { partial[2 * blockIdx.x] = sE; partial[2 * blockIdx.x + 1] = sB; }
+    const GBuf<double> Pt{partial, 2LL * gridDim.x};
+    if (threadIdx.x == 0) { Pt[2 * blockIdx.x] = sE; Pt[2 * blockIdx.x + 1] = sB; }
 }
 
 // partial[b][0] = max |k^ . F|, partial[b][1] = max |F| over this block's modes
@@ -63,13 +65,14 @@ divergence_kernel(const cplx<T>* __restrict__ F, GridGeom g, const T* __restrict
     T md2 = 0, mf2 = 0;                                // squared maxima
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int iy = row % g.Ny, iz = row / g.Ny;
-        const T b = ky[iy], c = kz[iz];
+        const T b = ky[PSATD_IX(iy, g.Ny)], c = kz[PSATD_IX(iz, g.Nz)];
         const size_t base = (size_t)row * g.Nx;
         for (int ix = threadIdx.x; ix < g.Nx; ix += blockDim.x) {
-            const T a = kx[ix];
+            const T a = kx[PSATD_IX(ix, g.Nx)];
             const T k2 = a * a + b * b + c * c;
             const size_t i = base + ix;
-            const cplx<T> X = F[i], Y = F[n + i], Z = F[2 * n + i];
+            const GBuf<const cplx<T>> S3{F, 3LL * (long long)n};
+            const cplx<T> X = S3[i], Y = S3[n + i], Z = S3[2 * n + i];
             const T dr = a * X.x + b * Y.x + c * Z.x;
             const T di = a * X.y + b * Y.y + c * Z.y;
             if (k2 > T(0)) md2 = max(md2, (dr * dr + di * di) / k2);
@@ -78,7 +81,8 @@ divergence_kernel(const cplx<T>* __restrict__ F, GridGeom g, const T* __restrict
     }
     const double bd = block_max(sqrt((double)md2), sh);
     const double bf = block_max(sqrt((double)mf2), sh);
-    if (threadIdx.x == 0) { partial[2 * blockIdx.x] = bd; partial[2 * blockIdx.x + 1] = bf; }
+    const GBuf<double> Pt{partial, 2LL * gridDim.x};
+    if (threadIdx.x == 0) { Pt[2 * blockIdx.x] = bd; Pt[2 * blockIdx.x + 1] = bf; }
 }
 
 __global__ void reduce_final_kernel(const double* __restrict__ partial, int nblocks, int width, int nsum,
@@ -88,11 +92,11 @@ __global__ void reduce_final_kernel(const double* __restrict__ partial, int nblo
         const bool is_sum = col < nsum;
         double v = 0.0;
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-            const double x = partial[(size_t)b * width + col];
+            const double x = partial[PSATD_IX((size_t)b * width + col, (long long)nblocks * width)];
             v = is_sum ? v + x : fmax(v, x);
         }
         const double r = is_sum ? block_sum(v, sh) : block_max(v, sh);
-        if (threadIdx.x == 0) out[col] = r;
+        if (threadIdx.x == 0) out[PSATD_IX(col, width)] = r;
         __syncthreads();
     }
 }

@@ -52,8 +52,9 @@ energy_partials_kernel(const cplx<T>* __restrict__ f, long long n, double* __res
     const long long end = min(begin + kCellsPerPartial, n);
     double eE = 0.0, eB = 0.0;
     for (long long i = begin + threadIdx.x; i < end; i += kThreads) {
-        eE += cell_energy3<T>(f[i], f[n + i], f[2 * n + i]);
-        eB += cell_energy3<T>(f[3 * n + i], f[4 * n + i], f[5 * n + i]);
+        eE += cell_energy3<T>(f[PSATD_IX(i, 6 * n)], f[PSATD_IX(n + i, 6 * n)], f[PSATD_IX(2 * n + i, 6 * n)]);
+        eB += cell_energy3<T>(f[PSATD_IX(3 * n + i, 6 * n)], f[PSATD_IX(4 * n + i, 6 * n)],
+                              f[PSATD_IX(5 * n + i, 6 * n)]);
     }
     eE = warp_sum(eE);
     eB = warp_sum(eB);
@@ -63,8 +64,8 @@ energy_partials_kernel(const cplx<T>* __restrict__ f, long long n, double* __res
     if (threadIdx.x == 0) {
         double tE = 0.0, tB = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) { tE += sE[w]; tB += sB[w]; }
-        partial[2 * blockIdx.x] = tE;
-        partial[2 * blockIdx.x + 1] = tB;
+        partial[PSATD_IX(2 * blockIdx.x, 2 * kMaxPartials)] = tE;
+        partial[PSATD_IX(2 * blockIdx.x + 1, 2 * kMaxPartials)] = tB;
     }
 }
 
@@ -74,8 +75,8 @@ energy_final_kernel(const double* __restrict__ partial, int nparts, double* __re
     __shared__ double sE[kThreads / 32], sB[kThreads / 32];
     double eE = 0.0, eB = 0.0;
     for (int b = threadIdx.x; b < nparts; b += kThreads) {
-        eE += partial[2 * b];
-        eB += partial[2 * b + 1];
+        eE += partial[PSATD_IX(2 * b, 2 * kMaxPartials)];
+        eB += partial[PSATD_IX(2 * b + 1, 2 * kMaxPartials)];
     }
     eE = warp_sum(eE);
     eB = warp_sum(eB);

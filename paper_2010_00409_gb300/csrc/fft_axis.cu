@@ -31,16 +31,17 @@ fft_axis_kernel(cplx<T>* __restrict__ data, int axis, int Nx, int Ny, int Nz, in
         const long long row0 = (long long)blockIdx.x * W;
         const int nrow = (int)min((long long)W, rows - row0);
         cplx<T>* base = data + row0 * Nx;
+        const GBuf<cplx<T>> F{data, rows * Nx};
         const FastDiv dn = fast_div(Nx);
         for (int e = tid; e < nrow * Nx; e += nthr) {
             const int w = fdiv(e, dn), n = e - w * Nx;
-            A[w * P + pad32(n)] = base[e];
+            A[w * P + pad32(n)] = F.at(base, e);
         }
         __syncthreads();
         cplx<T>* res = fft_tile<T, S>(A, B, pl, nrow, P, tw);
         for (int e = tid; e < nrow * Nx; e += nthr) {
             const int w = fdiv(e, dn), n = e - w * Nx;
-            base[e] = res[w * P + pad32(n)];
+            F.at(base, e) = res[w * P + pad32(n)];
         }
         return;
     }
@@ -57,16 +58,17 @@ fft_axis_kernel(cplx<T>* __restrict__ data, int axis, int Nx, int Ny, int Nz, in
     const int nw = min(W, Nx - x0);
     const size_t stride = (axis == 1) ? (size_t)Nx : plane;
     cplx<T>* base = data + (size_t)comp * plane * Nz + (axis == 1 ? (size_t)o * plane : (size_t)o * Nx) + x0;
+    const GBuf<cplx<T>> F{data, (long long)ncomp * plane * Nz};
     const FastDiv dw = fast_div(nw);
     for (int e = tid; e < N * nw; e += nthr) {
         const int n = fdiv(e, dw), w = e - n * nw;
-        A[w * P + pad32(n)] = base[(size_t)n * stride + w];
+        A[w * P + pad32(n)] = F.at(base, (long long)n * stride + w);
     }
     __syncthreads();
     cplx<T>* res = fft_tile<T, S>(A, B, pl, nw, P, tw);
     for (int e = tid; e < N * nw; e += nthr) {
         const int n = fdiv(e, dw), w = e - n * nw;
-        base[(size_t)n * stride + w] = res[w * P + pad32(n)];
+        F.at(base, (long long)n * stride + w) = res[w * P + pad32(n)];
     }
 }
 

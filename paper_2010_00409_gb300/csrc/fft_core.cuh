@@ -199,7 +199,7 @@ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in, cp
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const cplx<T> wv = tw[(r * k) * tstride];
+                const cplx<T> wv = tw[PSATD_IX((r * k) * tstride, N)];
                 v[r] = (S < 0) ? cmul(v[r], wv) : cmulc(v[r], wv);
             }
         }

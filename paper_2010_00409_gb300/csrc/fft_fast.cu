@@ -53,10 +53,11 @@ fft_rows_kernel(cplx<T>* __restrict__ data, long long rows, const cplx<T>* __res
     const unsigned lane0 = (threadIdx.x & 31u) & ~(unsigned)(N2 - 1);
     const unsigned gmask = N2 >= 32 ? 0xffffffffu : (((1u << N2) - 1u) << lane0);
     cplx<T>* p = data + row * N;
+    const GBuf<cplx<T>> F{data, rows * N};
     cplx<T>* sc = scratch + g * N1 * RS;
     cplx<T> v[N1];
     if constexpr (S < 0) {
-        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = p[j + N2 * decltype(nc)::value]; });
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = F.at(p, j + N2 * decltype(nc)::value); });
         stage_a_fwd<T, S, N1, N2>(v, j, tw);
         xscatter<T, N1, N2, RS, 1>(v, sc, j);
         __syncwarp(gmask);
@@ -65,7 +66,7 @@ fft_rows_kernel(cplx<T>* __restrict__ data, long long rows, const cplx<T>* __res
             constexpr int q = decltype(qc)::value;
             static_for<0, N2>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                p[(j + N2 * q) + N1 * k2] = v[q * N2 + k2];
+                F.at(p, (j + N2 * q) + N1 * k2) = v[q * N2 + k2];
             });
         });
     } else {
@@ -73,13 +74,13 @@ fft_rows_kernel(cplx<T>* __restrict__ data, long long rows, const cplx<T>* __res
             constexpr int q = decltype(qc)::value;
             static_for<0, N2>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                v[q * N2 + k2] = p[(j + N2 * q) + N1 * k2];
+                v[q * N2 + k2] = F.at(p, (j + N2 * q) + N1 * k2);
             });
         });
         xscatter_inv<T, S, N1, N2, RS, 1>(v, sc, j, tw);
         __syncwarp(gmask);
         xgather_inv<T, S, N1, N2, RS, 1>(v, sc, j);
-        static_for<0, N1>([&](auto nc) { p[j + N2 * decltype(nc)::value] = v[decltype(nc)::value]; });
+        static_for<0, N1>([&](auto nc) { F.at(p, j + N2 * decltype(nc)::value) = v[decltype(nc)::value]; });
     }
 }
 
@@ -102,10 +103,11 @@ fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, co
     const int comp = (int)(rest / outerN);
     const size_t stride = axis == 1 ? (size_t)Nx : plane;
     cplx<T>* base = data + (size_t)comp * plane * Nz + (axis == 1 ? (size_t)o * plane : (size_t)o * Nx) + (size_t)t * W + c;
+    const GBuf<cplx<T>> F{data, (long long)(gridDim.x / (ntile * outerN)) * plane * Nz};
     cplx<T>* sc = scratch + c;
     cplx<T> v[N1];
     if constexpr (S < 0) {
-        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = base[(j + N2 * decltype(nc)::value) * stride]; });
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = F.at(base, (long long)(j + N2 * decltype(nc)::value) * stride); });
         stage_a_fwd<T, S, N1, N2>(v, j, tw);
         xscatter<T, N1, N2, RS, ES>(v, sc, j);
         __syncthreads();
@@ -114,7 +116,7 @@ fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, co
             constexpr int q = decltype(qc)::value;
             static_for<0, N2>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                base[((j + N2 * q) + N1 * k2) * stride] = v[q * N2 + k2];
+                F.at(base, (long long)((j + N2 * q) + N1 * k2) * stride) = v[q * N2 + k2];
             });
         });
     } else {
@@ -122,13 +124,13 @@ fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, co
             constexpr int q = decltype(qc)::value;
             static_for<0, N2>([&](auto kc) {
                 constexpr int k2 = decltype(kc)::value;
-                v[q * N2 + k2] = base[((j + N2 * q) + N1 * k2) * stride];
+                v[q * N2 + k2] = F.at(base, (long long)((j + N2 * q) + N1 * k2) * stride);
             });
         });
         xscatter_inv<T, S, N1, N2, RS, ES>(v, sc, j, tw);
         __syncthreads();
         xgather_inv<T, S, N1, N2, RS, ES>(v, sc, j);
-        static_for<0, N1>([&](auto nc) { base[(j + N2 * decltype(nc)::value) * stride] = v[decltype(nc)::value]; });
+        static_for<0, N1>([&](auto nc) { F.at(base, (long long)(j + N2 * decltype(nc)::value) * stride) = v[decltype(nc)::value]; });
     }
 }
 
@@ -154,13 +156,14 @@ kspace_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __
     const int y = blockIdx.x / ntile;
     const int ix = xt * W + c;
     cplx<T>* base = data + (size_t)y * Nx + ix;
+    const GBuf<cplx<T>> F{data, 6LL * (long long)cstride};
     cplx<T> v[N1];
 
     // forward z transforms: spectrum of component q -> slot q
     for (int q = 0; q < 6; ++q) {
         cplx<T>* p = base + q * cstride;
         cplx<T>* sl = spec + q * (Nz * W) + c;
-        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = p[(j + N2 * decltype(nc)::value) * plane]; });
+        static_for<0, N1>([&](auto nc) { v[decltype(nc)::value] = F.at(p, (long long)(j + N2 * decltype(nc)::value) * plane); });
         stage_a_fwd<T, -1, N1, N2>(v, j, tw);
         xscatter<T, N1, N2, RS, ES>(v, sl, j);
         __syncthreads();
@@ -180,17 +183,18 @@ kspace_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __
     {
         const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
         const int ax = min(ix, Nx - ix), ay = min(y, Ny - y);
-        const T kx = kxs[ix], ky = kys[y];
+        const T kx = kxs[PSATD_IX(ix, Nx)], ky = kys[PSATD_IX(y, Ny)];
+        const long long ncoef = (long long)(Nz / 2 + 1) * Nyh * Nxh;
         cplx<T>* sl = spec + c;
 #pragma unroll 4
         for (int s = 0; s < N1; ++s) {
             const int iz = j + N2 * s;
             const int az = min(iz, Nz - iz);
-            const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
+            const ModeCoef<T> m = coef[PSATD_IX(((size_t)az * Nyh + ay) * Nxh + ax, ncoef)];
             const int o = iz * W;
             cplx<T> Ex = sl[o], Ey = sl[Nz * W + o], Ez = sl[2 * Nz * W + o];
             cplx<T> Bx = sl[3 * Nz * W + o], By = sl[4 * Nz * W + o], Bz = sl[5 * Nz * W + o];
-            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzs[iz] * m.kinv, m.C, m.S);
+            rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, kx * m.kinv, ky * m.kinv, kzs[PSATD_IX(iz, Nz)] * m.kinv, m.C, m.S);
             sl[o] = Ex; sl[Nz * W + o] = Ey; sl[2 * Nz * W + o] = Ez;
             sl[3 * Nz * W + o] = Bx; sl[4 * Nz * W + o] = By; sl[5 * Nz * W + o] = Bz;
         }
@@ -212,7 +216,7 @@ kspace_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __
         __syncthreads();
         xgather_inv<T, +1, N1, N2, RS, ES>(v, sl, j);
         cplx<T>* p = base + q * cstride;
-        static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[decltype(nc)::value]; });
+        static_for<0, N1>([&](auto nc) { F.at(p, (long long)(j + N2 * decltype(nc)::value) * plane) = v[decltype(nc)::value]; });
     }
 }
 

@@ -160,8 +160,13 @@ __host__ __device__ __forceinline__ void reg_dft(cplx<T> (&v)[N]) {
 // Pencil stages.  tw[t] = exp(-2 pi i t / N) (inverse uses the conjugate).
 // ---------------------------------------------------------------------------
 template <typename T, int S>
-__host__ __device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int idx) {
+__host__ __device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int idx, int n) {
+#ifdef __CUDA_ARCH__
+    const cplx<T> w = tw[PSATD_IX(idx, n)];          // the table holds n = N entries
+#else
+    (void)n;
     const cplx<T> w = tw[idx];
+#endif
     return S < 0 ? w : mk<T>(w.x, -w.y);
 }
 
@@ -171,7 +176,7 @@ __host__ __device__ __forceinline__ void stage_a_fwd(cplx<T> (&v)[N1], int j, co
     reg_dft<T, S, N1>(v);
     static_for<1, N1>([&](auto kc) {
         constexpr int k1 = decltype(kc)::value;
-        if (j) v[k1] = cmul(v[k1], twiddle<T, S>(tw, j * k1));
+        if (j) v[k1] = cmul(v[k1], twiddle<T, S>(tw, j * k1, N1 * N2));
     });
 }
 
@@ -212,7 +217,7 @@ __host__ __device__ __forceinline__ void stage_a_inv_scatter(cplx<T> (&v)[N1], c
         cplx<T>* row = sc + k1 * (N2 + 1);
         static_for<0, N2>([&](auto nc) {
             constexpr int n2 = decltype(nc)::value;
-            row[n2] = (n2 == 0 || k1 == 0) ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1));
+            row[n2] = (n2 == 0 || k1 == 0) ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1, N1 * N2));
         });
     });
 }
@@ -286,7 +291,7 @@ __device__ __forceinline__ void xscatter_inv(cplx<T> (&v)[N1], cplx<T>* sc, int 
         cplx<T>* row = sc + k1 * RS;
         static_for<0, N2>([&](auto nc) {
             constexpr int n2 = decltype(nc)::value;
-            row[n2 * ES] = (n2 == 0) ? w[n2] : (k1 == 0 ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1)));
+            row[n2 * ES] = (n2 == 0) ? w[n2] : (k1 == 0 ? w[n2] : cmul(w[n2], twiddle<T, S>(tw, n2 * k1, N1 * N2)));
         });
     });
 }

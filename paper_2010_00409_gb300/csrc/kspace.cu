@@ -76,12 +76,13 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     const size_t cstride = plane * Nz;
     const size_t comp_tile = (size_t)W * P;
     cplx<T>* base = data + (size_t)y * Nx + x0;
+    const GBuf<cplx<T>> G{data, 6LL * (long long)cstride};
 
     const FastDiv dw = fast_div(nw), dz = fast_div(Nz);
     for (int c = 0; c < 6; ++c) {
         for (int e = tid; e < Nz * nw; e += nthr) {
             const int n = fdiv(e, dw), w = e - n * nw;
-            F[c * comp_tile + w * P + pad32(n)] = base[c * cstride + (size_t)n * plane + w];
+            F[c * comp_tile + w * P + pad32(n)] = G.at(base, c * cstride + (size_t)n * plane + w);
         }
     }
     __syncthreads();
@@ -102,8 +103,8 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
         const int w = fdiv(e, dz), n = e - w * Nz;
         const int ix = x0 + w;
         const int ax = min(ix, Nx - ix), az = min(n, Nz - n);
-        const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
-        const T nxv = kx[ix] * m.kinv, nyv = ky[y] * m.kinv, nzv = kz[n] * m.kinv;
+        const ModeCoef<T> m = coef[PSATD_IX(((size_t)az * Nyh + ay) * Nxh + ax, (long long)(Nz / 2 + 1) * Nyh * Nxh)];
+        const T nxv = kx[PSATD_IX(ix, Nx)] * m.kinv, nyv = ky[PSATD_IX(y, Ny)] * m.kinv, nzv = kz[PSATD_IX(n, Nz)] * m.kinv;
         const size_t o = (size_t)w * P + pad32(n);
         mode_update<T>(F + o, F + comp_tile + o, F + 2 * comp_tile + o, F + 3 * comp_tile + o,
                        F + 4 * comp_tile + o, F + 5 * comp_tile + o, nxv, nyv, nzv, m.C, m.S, mode,
@@ -124,7 +125,7 @@ kspace_z_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int W, int P
     for (int c = 0; c < 6; ++c) {
         for (int e = tid; e < Nz * nw; e += nthr) {
             const int n = fdiv(e, dw), w = e - n * nw;
-            base[c * cstride + (size_t)n * plane + w] = F[c * comp_tile + w * P + pad32(n)];
+            G.at(base, c * cstride + (size_t)n * plane + w) = F[c * comp_tile + w * P + pad32(n)];
         }
     }
 }
@@ -144,10 +145,11 @@ modes_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, const T* __rest
         const size_t r = e / Nx;
         const int iy = (int)(r % Ny), iz = (int)(r / Ny);
         const int ax = min(ix, Nx - ix), ay = min(iy, Ny - iy), az = min(iz, Nz - iz);
-        const ModeCoef<T> m = coef[((size_t)az * Nyh + ay) * Nxh + ax];
-        mode_update<T>(data + e, data + n + e, data + 2 * n + e, data + 3 * n + e, data + 4 * n + e,
-                       data + 5 * n + e, kx[ix] * m.kinv, ky[iy] * m.kinv, kz[iz] * m.kinv, m.C, m.S, mode,
-                       scale);
+        const ModeCoef<T> m = coef[PSATD_IX(((size_t)az * Nyh + ay) * Nxh + ax, (long long)(Nz / 2 + 1) * Nyh * Nxh)];
+        const GBuf<cplx<T>> G{data, 6LL * (long long)n};
+        mode_update<T>(&G[e], &G[n + e], &G[2 * n + e], &G[3 * n + e], &G[4 * n + e], &G[5 * n + e],
+                       kx[PSATD_IX(ix, Nx)] * m.kinv, ky[PSATD_IX(iy, Ny)] * m.kinv, kz[PSATD_IX(iz, Nz)] * m.kinv,
+                       m.C, m.S, mode, scale);
     }
 }
 

@@ -108,10 +108,11 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     // r = h NM .. h NM + NM - 1 of position (c, j)); their loads complete while
     // the tile copies fly
     cplx<T> twr[N1];
-    static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[j * decltype(kc)::value]; });
+    static_for<1, N1>([&](auto kc) { twr[decltype(kc)::value] = tw[PSATD_IX(j * decltype(kc)::value, Nz)]; });
     const int Nxh = coef_nx, Nyh = Ny / 2 + 1;
     const int ax = HALF ? (nq ? coef_nx - 1 : ix) : min(ix, Nx - ix), ay = min(y, Ny - y);
-    const T kx = nq ? kx_nyq : kxs[ix], ky = kys[y];
+    const T kx = nq ? kx_nyq : kxs[PSATD_IX(ix, Nx)], ky = kys[PSATD_IX(y, Ny)];
+    const long long ncoef = (long long)(Nz / 2 + 1) * Nyh * Nxh;
     ModeCoef<T> mc[NM];
     T kzr[NM];
     static_for<0, NM>([&](auto mcix) {
@@ -119,8 +120,8 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
         const int r = h * NM + m;
         const int iz = (j + N2 * (r / N2)) + N1 * (r % N2);
         const int az = min(iz, Nz - iz);
-        mc[m] = coef[((size_t)az * Nyh + ay) * Nxh + ax];
-        kzr[m] = kzs[iz];
+        mc[m] = coef[PSATD_IX(((size_t)az * Nyh + ay) * Nxh + ax, ncoef)];
+        kzr[m] = kzs[PSATD_IX(iz, Nz)];
     });
 
     pdl_wait();
@@ -241,6 +242,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
     if constexpr (G > 1) __syncthreads();                      // the inverse reads the other group's modes
 
     cplx<T>* base = nq ? nyq + y : data + (size_t)y * Nx + ix;
+    const GBuf<cplx<T>> F = nq ? GBuf<cplx<T>>{nyq, 6LL * Ny * Nz} : GBuf<cplx<T>>{data, 6LL * Nx * Ny * Nz};
     if constexpr (SPECTRAL_OUT) {
         // store the updated spectrum in natural kz order (one-shot focal path)
         for (int q = NC * h; q < NC * h + NC; ++q) {
@@ -250,7 +252,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                 constexpr int qq = decltype(qc)::value;
                 static_for<0, N2>([&](auto kc) {
                     constexpr int k2 = decltype(kc)::value;
-                    p[(size_t)((j + N2 * qq) + N1 * k2) * plane] = sl[(qq * N2 + k2) * RP];
+                    F.at(p, (long long)((j + N2 * qq) + N1 * k2) * plane) = sl[(qq * N2 + k2) * RP];
                 });
             });
         }
@@ -284,7 +286,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
                     cplx<T> val = w[n2];
                     if (n2 > 0 && k1 > 0) {
                         // W_N^{-n2 k1}; for q = 0 this is conj(twr[n2]) (k1 = j)
-                        const cplx<T> tv = (q == 0) ? twr[n2] : tw[n2 * k1];
+                        const cplx<T> tv = (q == 0) ? twr[n2] : tw[PSATD_IX(n2 * k1, Nz)];
                         val = cmulc(val, tv);
                     }
                     ((n2 & 1) ? od : ev)[n2 * W] = val;
@@ -305,7 +307,7 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
             constexpr int b = decltype(bc)::value;
             reg_dft<T, +1, N1>(v[b]);
             cplx<T>* p = base + (q0 + b) * cstride;
-            static_for<0, N1>([&](auto nc) { p[(j + N2 * decltype(nc)::value) * plane] = v[b][decltype(nc)::value]; });
+            static_for<0, N1>([&](auto nc) { F.at(p, (long long)(j + N2 * decltype(nc)::value) * plane) = v[b][decltype(nc)::value]; });
         });
     }
     drain();

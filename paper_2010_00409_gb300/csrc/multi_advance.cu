@@ -87,17 +87,18 @@ __device__ void x_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* A = sm;
     cplx<T>* B = sm + (size_t)W * Pp;
     cplx<T>* base = P.f + row0 * Nx;
+    const GBuf<cplx<T>> F{P.f, rows * Nx};
     const int n = nrow * Nx;
     const FastDiv dn = fast_div(Nx);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int w = fdiv(e, dn), i = e - w * Nx;
-        A[w * Pp + pad32(i)] = __ldcg(base + e);
+        A[w * Pp + pad32(i)] = __ldcg(&F.at(base, e));
     }
     __syncthreads();
     const cplx<T>* res = fft_tile<T, S>(A, B, P.plan[0], nrow, Pp, P.tw[0]);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int w = fdiv(e, dn), i = e - w * Nx;
-        base[e] = res[w * Pp + pad32(i)];
+        F.at(base, e) = res[w * Pp + pad32(i)];
     }
 }
 
@@ -114,17 +115,18 @@ __device__ void y_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* A = sm;
     cplx<T>* B = sm + (size_t)W * Pp;
     cplx<T>* base = P.f + (size_t)comp * plane * Nz + (size_t)z * plane + x0;
+    const GBuf<cplx<T>> F{P.f, 6LL * (long long)plane * Nz};
     const int n = Ny * nw;
     const FastDiv dw = fast_div(nw);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int r = fdiv(e, dw), w = e - r * nw;
-        A[w * Pp + pad32(r)] = __ldcg(base + (size_t)r * Nx + w);
+        A[w * Pp + pad32(r)] = __ldcg(&F.at(base, (long long)r * Nx + w));
     }
     __syncthreads();
     const cplx<T>* res = fft_tile<T, S>(A, B, P.plan[1], nw, Pp, P.tw[1]);
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int r = fdiv(e, dw), w = e - r * nw;
-        base[(size_t)r * Nx + w] = res[w * Pp + pad32(r)];
+        F.at(base, (long long)r * Nx + w) = res[w * Pp + pad32(r)];
     }
 }
 
@@ -151,27 +153,30 @@ __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     cplx<T>* F = sm;                                          // [6][W][Pp]
     cplx<T>* scratch = sm + 6 * ct;                           // [W][Pp]
     cplx<T>* base = P.f + (size_t)y * Nx + x0;
+    const GBuf<cplx<T>> G{P.f, 6LL * (long long)cstride};
     const int n = Nz * nw;
     const FastDiv dw = fast_div(nw), dz = fast_div(Nz);
     for (int c = 0; c < 6; ++c)
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
             const int r = fdiv(e, dw), w = e - r * nw;
-            F[c * ct + w * Pp + pad32(r)] = __ldcg(base + c * cstride + (size_t)r * plane + w);
+            F[c * ct + w * Pp + pad32(r)] = __ldcg(&G.at(base, c * cstride + (size_t)r * plane + w));
         }
     __syncthreads();
     for (int c = 0; c < 6; ++c) z_transform<T, -1>(F + c * ct, scratch, P, nw, Pp);
 
     const int Nxh = Nx / 2 + 1, Nyh = Ny / 2 + 1;
     const int ay = min(y, Ny - y);
-    const T ky = P.k[1][y];
+    const T ky = P.k[1][PSATD_IX(y, Ny)];
+    const long long ncoef = (long long)(Nz / 2 + 1) * Nyh * Nxh;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const int w = fdiv(e, dz), r = e - w * Nz;
         const int ix = x0 + w;
         const int ax = min(ix, Nx - ix), az = min(r, Nz - r);
-        const ModeCoef<T> m = P.coef[((size_t)az * Nyh + ay) * Nxh + ax];
+        const ModeCoef<T> m = P.coef[PSATD_IX(((size_t)az * Nyh + ay) * Nxh + ax, ncoef)];
         cplx<T>* o = F + w * Pp + pad32(r);
         cplx<T> Ex = o[0], Ey = o[ct], Ez = o[2 * ct], Bx = o[3 * ct], By = o[4 * ct], Bz = o[5 * ct];
-        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, P.k[0][ix] * m.kinv, ky * m.kinv, P.k[2][r] * m.kinv, m.C, m.S);
+        rotate_mode<T>(Ex, Ey, Ez, Bx, By, Bz, P.k[0][PSATD_IX(ix, Nx)] * m.kinv, ky * m.kinv,
+                       P.k[2][PSATD_IX(r, Nz)] * m.kinv, m.C, m.S);
         o[0] = Ex; o[ct] = Ey; o[2 * ct] = Ez;
         o[3 * ct] = Bx; o[4 * ct] = By; o[5 * ct] = Bz;
     }
@@ -181,7 +186,7 @@ __device__ void z_tile(const MultiProblem<T>& P, long long item, cplx<T>* sm) {
     for (int c = 0; c < 6; ++c)
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
             const int r = fdiv(e, dw), w = e - r * nw;
-            base[c * cstride + (size_t)r * plane + w] = F[c * ct + w * Pp + pad32(r)];
+            G.at(base, c * cstride + (size_t)r * plane + w) = F[c * ct + w * Pp + pad32(r)];
         }
 }
 
@@ -214,7 +219,7 @@ multi_advance_kernel(const MultiProblem<T>* __restrict__ probs, const long long*
                 int lo = 0, hi = nprob - 1;                     // the box p with pre[p] <= g < pre[p + 1]
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (pre[mid] <= g) lo = mid;
+                    if (pre[PSATD_IX(mid, nprob + 1)] <= g) lo = mid;
                     else hi = mid - 1;
                 }
                 if (lo != cur) {

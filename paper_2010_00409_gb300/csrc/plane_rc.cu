@@ -116,10 +116,11 @@ __device__ __forceinline__ void c2r_pair(float2 X, float2 P, float2 w, float2* a
 // r2c phase 1 compute: stage A over n1 of the row segment in v (lane j holds
 // z[j + 8 n1]) and the twiddles W_128^{j k1}.
 __device__ __forceinline__ void r2c_stage_a(float2 (&v)[16], int j, const float2* __restrict__ twx) {
+    const GBuf<const float2> TX{twx, 256};
     reg_dft<float, -1, 16>(v);
     static_for<1, 16>([&](auto kc) {
         constexpr int k1 = decltype(kc)::value;
-        if (j) v[k1] = cmul(v[k1], twx[2 * j * k1]);
+        if (j) v[k1] = cmul(v[k1], TX[2 * j * k1]);
     });
 }
 
@@ -138,7 +139,9 @@ __device__ __forceinline__ void r2c_scatter(const float2 (&v)[16], cg::cluster_g
 // column to nq.
 __device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, int tid, const float2* __restrict__ twx,
                                             const float2* __restrict__ twy, float2* __restrict__ plane,
-                                            float2* __restrict__ nq) {
+                                            float2* __restrict__ nq, const GBuf<float2>& F,
+                                            const GBuf<float2>& NQ) {
+    const GBuf<const float2> TX{twx, 256};
     // ---------------- phase 2a: stage B and the r2c pairing, one row per thread
     {
         const int y = tid;
@@ -163,7 +166,7 @@ __device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, i
         } else {
             static_for<0, 8>([&](auto kc) {            // k = r + 16 k2 pairs with (16 - r) + 16 (7 - k2)
                 constexpr int k2 = decltype(kc)::value;
-                r2c_pair(a[0][k2], a[1][7 - k2], twx[r + 16 * k2], &a[0][k2], &a[1][7 - k2]);
+                r2c_pair(a[0][k2], a[1][7 - k2], TX[r + 16 * k2], &a[0][k2], &a[1][7 - k2]);
             });
         }
         static_for<0, 2>([&](auto sc) {
@@ -193,14 +196,14 @@ __device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, i
                     const int ky = jy + 16 * k2;
                     const float2 P = v[k2], Pm = col0[(kNy - ky) & (kNy - 1)];
                     v[k2] = make_float2(0.5f * (P.x + Pm.x), 0.5f * (P.y - Pm.y));
-                    nq[ky] = make_float2(0.5f * (P.y + Pm.y), -0.5f * (P.x - Pm.x));
+                    NQ.at(nq, ky) = make_float2(0.5f * (P.y + Pm.y), -0.5f * (P.x - Pm.x));
                 });
             }
         }
         float2* out = plane + 16 * r + c;
         static_for<0, 16>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
-            st_field(out + (size_t)(jy + 16 * k2) * kM, v[k2]);
+            st_field(&F.at(out, (long long)(jy + 16 * k2) * kM), v[k2]);
         });
     }
 }
@@ -209,11 +212,13 @@ __device__ __forceinline__ void r2c_columns(float2* tile, float2* col0, int r, i
 // slot 16 r + c at rows jy + 16 k2), block 0 repacks slot 0 as S0 + i SN first;
 // the column results end in the tile as [row][column].
 __device__ __forceinline__ void c2r_columns(float2 (&v)[16], float2* tile, int r, int c, int jy,
-                                            const float2* __restrict__ twy, const float2* __restrict__ nq) {
+                                            const float2* __restrict__ twy, const float2* __restrict__ nq,
+                                            const GBuf<const float2>& NQ) {
+    const GBuf<const float2> TY{twy, 256};
     if (r == 0 && c == 0) {                            // repack slot 0: S0 + i SN
         static_for<0, 16>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
-            const float2 sn = nq[jy + 16 * k2];
+            const float2 sn = NQ.at(nq, jy + 16 * k2);
             v[k2] = make_float2(v[k2].x - sn.y, v[k2].y + sn.x);
         });
     }
@@ -221,7 +226,7 @@ __device__ __forceinline__ void c2r_columns(float2 (&v)[16], float2* tile, int r
     static_for<0, 16>([&](auto nc) {
         constexpr int n2 = decltype(nc)::value;
         float2 val = v[n2];
-        if (n2 > 0 && jy > 0) val = cmulc(val, twy[n2 * jy]);
+        if (n2 > 0 && jy > 0) val = cmulc(val, TY[n2 * jy]);
         tile[sw16(16 * jy + n2, c)] = val;              // element (k1 = jy, n2)
     });
     __syncthreads();
@@ -235,6 +240,7 @@ __device__ __forceinline__ void c2r_columns(float2 (&v)[16], float2* tile, int r
 // barrier that frees every block's tile).
 __device__ __forceinline__ void c2r_rows(float2* tile, cg::cluster_group& cluster, int r, int tid,
                                          const float2* __restrict__ twx) {
+    const GBuf<const float2> TX{twx, 256};
     const int y = tid;
     float2 x[2][8];
     static_for<0, 2>([&](auto sc) {
@@ -256,7 +262,7 @@ __device__ __forceinline__ void c2r_rows(float2* tile, cg::cluster_group& cluste
     } else {
         static_for<0, 8>([&](auto kc) {
             constexpr int k2 = decltype(kc)::value;
-            c2r_pair(x[0][k2], x[1][7 - k2], twx[r + 16 * k2], &z[0][k2], &z[1][7 - k2]);
+            c2r_pair(x[0][k2], x[1][7 - k2], TX[r + 16 * k2], &z[0][k2], &z[1][7 - k2]);
         });
     }
     const int k1s[2] = {r == 0 ? 0 : r, r == 0 ? 8 : 16 - r};
@@ -266,7 +272,7 @@ __device__ __forceinline__ void c2r_rows(float2* tile, cg::cluster_group& cluste
         const int k1 = k1s[s];
         static_for<1, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            if (k1) z[s][j] = cmulc(z[s][j], twx[2 * j * k1]);
+            if (k1) z[s][j] = cmulc(z[s][j], TX[2 * j * k1]);
         });
     });
     cluster.barrier_wait();
@@ -284,14 +290,15 @@ __device__ __forceinline__ void c2r_rows(float2* tile, cg::cluster_group& cluste
 }
 
 // c2r phase 3: inverse stage A of the block's rows 32 r .. 32 r + 31, stored.
-__device__ __forceinline__ void c2r_stage_a_store(const float2* tile, int r, int tid, float2* __restrict__ plane) {
+__device__ __forceinline__ void c2r_stage_a_store(const float2* tile, int r, int tid, float2* __restrict__ plane,
+                                                  const GBuf<float2>& F) {
     const int w = tid >> 5, lane = tid & 31, g = lane >> 3, j = lane & 7;
     const int yl = w + 8 * g;
     float2 v[16];
     static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = tile[decltype(kc)::value * 256 + j * 32 + (yl ^ j)]; });
     reg_dft<float, +1, 16>(v);                         // v[n1] = z[j + 8 n1]
     float2* p = plane + (size_t)(32 * r + yl) * kM;
-    static_for<0, 16>([&](auto nc) { st_field(p + j + 8 * decltype(nc)::value, v[decltype(nc)::value]); });
+    static_for<0, 16>([&](auto nc) { st_field(&F.at(p, j + 8 * decltype(nc)::value), v[decltype(nc)::value]); });
 }
 
 constexpr size_t kTileBytes = (size_t)kM * kNy / kRcC * sizeof(float2);   // 32 KB
@@ -334,6 +341,8 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     const int pl = blockIdx.x / kRcC;
     float2* plane = data + (size_t)pl * (kM * kNy);
     const int tid = threadIdx.x;
+    const long long npl = gridDim.x / kRcC;
+    const GBuf<float2> F{data, npl * kM * kNy}, NQ{nyq, npl * kNy};
     pdl_wait();
     prefetch_plane(data, pl, r);
 
@@ -342,13 +351,13 @@ plane_r2c_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
         const int y = 32 * r + w + 8 * g;              // rows of a warp alternate in bit 3 (bank spread)
         const float2* p = plane + (size_t)y * kM;
         float2 v[16];
-        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = ld_field(p + j + 8 * decltype(nc)::value); });
+        static_for<0, 16>([&](auto nc) { v[decltype(nc)::value] = ld_field(&F.at(p, j + 8 * decltype(nc)::value)); });
         r2c_stage_a(v, j, twx);
         cluster.barrier_wait();
         r2c_scatter(v, cluster, tile, y, j);
     }
     cluster.sync();
-    r2c_columns(tile, col0, r, tid, twx, twy, plane, nyq + (size_t)pl * kNy);
+    r2c_columns(tile, col0, r, tid, twx, twy, plane, nyq + (size_t)pl * kNy, F, NQ);
 }
 
 // capped at 48 registers: five blocks per SM (the packed butterfly adds would
@@ -365,6 +374,9 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
     const int pl = blockIdx.x / kRcC;
     float2* plane = data + (size_t)pl * (kM * kNy);
     const int tid = threadIdx.x;
+    const long long npl = gridDim.x / kRcC;
+    const GBuf<float2> F{data, npl * kM * kNy};
+    const GBuf<const float2> NQ{nyq, npl * kNy};
     pdl_wait();
     prefetch_plane(data, pl, r);
 
@@ -372,13 +384,13 @@ plane_c2r_kernel(float2* __restrict__ data, const float2* __restrict__ twx, cons
         const int c = tid & 15, jy = tid >> 4;
         const float2* in = plane + 16 * r + c;
         float2 v[16];
-        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = ld_field(in + (size_t)(jy + 16 * decltype(kc)::value) * kM); });
-        c2r_columns(v, tile, r, c, jy, twy, nyq + (size_t)pl * kNy);
+        static_for<0, 16>([&](auto kc) { v[decltype(kc)::value] = ld_field(&F.at(in, (long long)(jy + 16 * decltype(kc)::value) * kM)); });
+        c2r_columns(v, tile, r, c, jy, twy, nyq + (size_t)pl * kNy, NQ);
     }
     __syncthreads();
     c2r_rows(tile, cluster, r, tid, twx);
     cluster.sync();
-    c2r_stage_a_store(tile, r, tid, plane);
+    c2r_stage_a_store(tile, r, tid, plane, F);
 }
 
 }  // namespace

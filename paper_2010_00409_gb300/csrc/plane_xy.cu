@@ -50,6 +50,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
     const int r = (int)cluster.block_rank();
     const long long plane_id = blockIdx.x / C;
     cplx<T>* plane = data + plane_id * (long long)(NX * NY);
+    const GBuf<cplx<T>> F{data, (long long)(gridDim.x / C) * NX * NY};
     pdl_wait();                                        // the previous kernel's output is read below
 
     // ---------------- phase 1: rows along x, exchange by lane transpose
@@ -61,7 +62,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
             const int y = r * ROWS + rr * G + g;
             const cplx<T>* p = plane + (long long)y * NX;
             if constexpr (S < 0) {
-                static_for<0, N1X>([&](auto nc) { v[decltype(nc)::value] = p[j + N2X * decltype(nc)::value]; });
+                static_for<0, N1X>([&](auto nc) { v[decltype(nc)::value] = F.at(p, j + N2X * decltype(nc)::value); });
                 stage_a_fwd<T, S, N1X, N2X>(v, j, twx);
                 lane_transpose16<T>(v, j);
                 reg_dft<T, S, N2X>(v);                   // v[k2] = X[j + 16 k2]
@@ -73,11 +74,11 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
                     dst[y * COLS + (x % COLS)] = v[k2];
                 });
             } else {
-                static_for<0, N2X>([&](auto kc) { v[decltype(kc)::value] = p[j + N1X * decltype(kc)::value]; });
+                static_for<0, N2X>([&](auto kc) { v[decltype(kc)::value] = F.at(p, j + N1X * decltype(kc)::value); });
                 reg_dft<T, S, N2X>(v);                   // over k2: v[n2] for k1 = j
                 static_for<1, N2X>([&](auto nc) {
                     constexpr int n2 = decltype(nc)::value;
-                    if (j) v[n2] = cmul(v[n2], twiddle<T, S>(twx, n2 * j));
+                    if (j) v[n2] = cmul(v[n2], twiddle<T, S>(twx, n2 * j, NX));
                 });
                 lane_transpose16<T>(v, j);
                 reg_dft<T, S, N1X>(v);                   // v[n1] = x[j + 16 n1]
@@ -113,7 +114,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
                     constexpr int q = decltype(qc)::value;
                     static_for<0, N2Y>([&](auto kc) {
                         constexpr int k2 = decltype(kc)::value;
-                        out[(long long)((j + N2Y * q) + N1Y * k2) * NX] = v[q * N2Y + k2];
+                        F.at(out, (long long)((j + N2Y * q) + N1Y * k2) * NX) = v[q * N2Y + k2];
                     });
                 });
             } else {
@@ -129,7 +130,7 @@ plane_xy_kernel(cplx<T>* __restrict__ data, const cplx<T>* __restrict__ twx, con
                 __syncthreads();
                 xgather_inv<T, S, N1Y, N2Y, RS, ES>(v, col, j);
                 static_for<0, N1Y>([&](auto nc) {
-                    out[(long long)(j + N2Y * decltype(nc)::value) * NX] = v[decltype(nc)::value];
+                    F.at(out, (long long)(j + N2Y * decltype(nc)::value) * NX) = v[decltype(nc)::value];
                 });
             }
         }

@@ -25,6 +25,10 @@ using namespace psatd;
 
 namespace psatd {
 
+#ifdef PSATD_DEBUG
+void debug_register_reader(long long (*reader)(long long*, long long*));
+#endif
+
 bool make_plan(int N, AxisPlan* p) {
     p->N = N;
     p->npass = 0;
@@ -168,6 +172,24 @@ long long g_alloc_live = 0;
 long long g_alloc_limit = -1;                     // -1: no cap
 std::atomic<int> g_inject_after{0};               // 0: nothing armed
 std::atomic<int> g_inject_error{0};
+
+#ifdef PSATD_DEBUG
+std::mutex g_dbg_mutex;
+std::vector<long long (*)(long long*, long long*)>& dbg_readers() {
+    static std::vector<long long (*)(long long*, long long*)> r;
+    return r;
+}
+#endif
+}  // namespace
+
+#ifdef PSATD_DEBUG
+void psatd::debug_register_reader(long long (*reader)(long long*, long long*)) {
+    std::lock_guard<std::mutex> lock(g_dbg_mutex);
+    dbg_readers().push_back(reader);
+}
+#endif
+
+namespace {
 
 cudaError_t lib_malloc(void** p, size_t bytes) {
     std::lock_guard<std::mutex> lock(g_alloc_mutex);
@@ -1743,6 +1765,31 @@ long long psatd_debug_alloc_live(void) {
 void psatd_debug_inject_cuda_error(int after_calls, int cuda_error) {
     g_inject_error.store(cuda_error);
     g_inject_after.store(after_calls > 0 ? after_calls : 0);
+}
+
+long long psatd_debug_bounds_report(long long* first_index, long long* first_bound) {
+#ifdef PSATD_DEBUG
+    std::lock_guard<std::mutex> lock(g_dbg_mutex);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    long long total = 0;
+    bool first = true;
+    for (auto fn : dbg_readers()) {
+        long long fi = 0, fb = 0;
+        const long long n = fn(&fi, &fb);
+        if (n < 0) return -1;
+        if (n > 0 && first) {
+            if (first_index) *first_index = fi;
+            if (first_bound) *first_bound = fb;
+            first = false;
+        }
+        total += n;
+    }
+    return total;
+#else
+    (void)first_index;
+    (void)first_bound;
+    return -2;
+#endif
 }
 
 }  // extern "C"

@@ -35,7 +35,7 @@ __device__ __forceinline__ double profile_ul(double zeta, const PulseParams& p, 
     int k = (int)s;
     if (k > p.prof_n - 2) k = p.prof_n - 2;
     const double t = s - k;
-    const double2 a0 = p.prof[k], a1 = p.prof[k + 1];
+    const double2 a0 = p.prof[PSATD_IX(k, p.prof_n)], a1 = p.prof[PSATD_IX(k + 1, p.prof_n)];
     const double ar = a0.x + t * (a1.x - a0.x), ai = a0.y + t * (a1.y - a0.y);
     return ar * cos(phase) - ai * sin(phase);
 }
@@ -143,9 +143,9 @@ __device__ __forceinline__ void pol_vectors_f(float X, float Y, float Z, float d
 
 // One field value: complex storage takes (v, 0), real float32 storage v.
 template <typename T, bool REAL>
-__device__ __forceinline__ void store_value(void* data, size_t i, T v) {
-    if constexpr (REAL) static_cast<float*>(data)[i] = (float)v;
-    else static_cast<cplx<T>*>(data)[i] = mk<T>(v, (T)0);
+__device__ __forceinline__ void store_value(void* data, size_t i, size_t n, T v) {
+    if constexpr (REAL) static_cast<float*>(data)[PSATD_IX(i, n)] = (float)v;
+    else static_cast<cplx<T>*>(data)[PSATD_IX(i, n)] = mk<T>(v, (T)0);
 }
 
 template <typename T, bool REAL>
@@ -184,8 +184,8 @@ __global__ void init_pulse_kernel(void* __restrict__ data, GridGeom g, ShellGeom
                 }
             }
             for (int a = 0; a < 3; ++a) {
-                store_value<T, REAL>(data, a * n_cells + idx, (T)E[a]);
-                store_value<T, REAL>(data, (3 + a) * n_cells + idx, (T)B[a]);
+                store_value<T, REAL>(data, a * n_cells + idx, 6 * n_cells, (T)E[a]);
+                store_value<T, REAL>(data, (3 + a) * n_cells + idx, 6 * n_cells, (T)B[a]);
             }
             continue;
         }
@@ -208,8 +208,8 @@ __global__ void init_pulse_kernel(void* __restrict__ data, GridGeom g, ShellGeom
             }
         }
         for (int a = 0; a < 3; ++a) {
-            store_value<T, REAL>(data, a * n_cells + idx, (T)E[a]);
-            store_value<T, REAL>(data, (3 + a) * n_cells + idx, (T)B[a]);
+            store_value<T, REAL>(data, a * n_cells + idx, 6 * n_cells, (T)E[a]);
+            store_value<T, REAL>(data, (3 + a) * n_cells + idx, 6 * n_cells, (T)B[a]);
         }
     }
 }

@@ -8,12 +8,12 @@ namespace {
 
 __global__ void widen_kernel(const float* __restrict__ in, float2* __restrict__ out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = make_float2(in[i], 0.f);
+        out[PSATD_IX(i, n)] = make_float2(in[PSATD_IX(i, n)], 0.f);
 }
 
 __global__ void narrow_kernel(const float2* __restrict__ in, float* __restrict__ out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = in[i].x;
+        out[PSATD_IX(i, n)] = in[PSATD_IX(i, n)].x;
 }
 
 unsigned elementwise_blocks(size_t n) {

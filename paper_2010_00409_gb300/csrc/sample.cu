@@ -53,15 +53,15 @@ __global__ void weights_kernel(GridGeom g, double x_phys, int ny, int nz, double
     if (tid < nwx) {
         double q = (x_phys - g.x_min) / D;
         const double xt = g.x_min + D * (q - floor(q));              // Eq. 13
-        wx[tid] = dirichlet_weight(xt - (g.x_min + tid * g.dx), g.Nx, g.dx);
+        wx[PSATD_IX(tid, nwx)] = dirichlet_weight(xt - (g.x_min + tid * g.dx), g.Nx, g.dx);
     } else if (tid < nwx + nwy) {
         const int e = tid - nwx, p = e / g.Ny, j = e - p * g.Ny;
         const double y = y0 + (y1 - y0) * p / ny;
-        wy[e] = dirichlet_weight(y - (g.y_min + j * g.dy), g.Ny, g.dy);
+        wy[PSATD_IX(e, nwy)] = dirichlet_weight(y - (g.y_min + j * g.dy), g.Ny, g.dy);
     } else if (tid < nwx + nwy + nwz) {
         const int e = tid - nwx - nwy, q = e / g.Nz, l = e - q * g.Nz;
         const double z = z0 + (z1 - z0) * q / nz;
-        wz[e] = dirichlet_weight(z - (g.z_min + l * g.dz), g.Nz, g.dz);
+        wz[PSATD_IX(e, nwz)] = dirichlet_weight(z - (g.z_min + l * g.dz), g.Nz, g.dz);
     }
 }
 
@@ -82,13 +82,13 @@ __global__ void spectral_weights_kernel(GridGeom g, double x_phys, int ny, int n
     if (tid < nwx) {
         double q = (x_phys - g.x_min) / D;
         const double xt = g.x_min + D * (q - floor(q));              // Eq. 13
-        wx[tid] = mode_phase(tid, g.Nx, g.dx, xt - g.x_min);
+        wx[PSATD_IX(tid, nwx)] = mode_phase(tid, g.Nx, g.dx, xt - g.x_min);
     } else if (tid < nwx + nwy) {
         const int e = tid - nwx, p = e / g.Ny, j = e - p * g.Ny;
-        wy[e] = mode_phase(j, g.Ny, g.dy, y0 + (y1 - y0) * p / ny - g.y_min);
+        wy[PSATD_IX(e, nwy)] = mode_phase(j, g.Ny, g.dy, y0 + (y1 - y0) * p / ny - g.y_min);
     } else if (tid < nwx + nwy + nwz) {
         const int e = tid - nwx - nwy, q = e / g.Nz, l = e - q * g.Nz;
-        wz[e] = mode_phase(l, g.Nz, g.dz, z0 + (z1 - z0) * q / nz - g.z_min);
+        wz[PSATD_IX(e, nwz)] = mode_phase(l, g.Nz, g.dz, z0 + (z1 - z0) * q / nz - g.z_min);
     }
 }
 
@@ -105,10 +105,11 @@ __global__ void contract_x_kernel(const cplx<T>* __restrict__ f, GridGeom g, Com
     const int a = (int)(warp / ((long long)g.Nz * g.Ny));
     const long long rl = warp - (long long)a * g.Nz * g.Ny;
     const cplx<T>* row = f + (size_t)cl.c[a] * g.Nx * g.Ny * g.Nz + (size_t)rl * g.Nx;
+    const GBuf<const cplx<T>> F{f, 6LL * g.Nx * g.Ny * g.Nz};
     double re = 0.0, im = 0.0;
     for (int i = lane; i < g.Nx; i += 32) {
-        const cplx<T> v = row[i];
-        const double2 w = wx[i];
+        const cplx<T> v = F.at(row, i);
+        const double2 w = wx[PSATD_IX(i, g.Nx)];
         re += w.x * (double)v.x - w.y * (double)v.y;
         im += w.x * (double)v.y + w.y * (double)v.x;
     }
@@ -116,7 +117,7 @@ __global__ void contract_x_kernel(const cplx<T>* __restrict__ f, GridGeom g, Com
         re += __shfl_down_sync(0xffffffffu, re, o);
         im += __shfl_down_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) out[warp] = make_double2(re, im);
+    if (lane == 0) out[PSATD_IX(warp, rows)] = make_double2(re, im);
 }
 
 // Real float32 fields: g[a][l][j] = sum_i wx[i] f[c_a][l][j][i] with real f.
@@ -129,10 +130,11 @@ __global__ void contract_x_real_kernel(const float* __restrict__ f, GridGeom g, 
     const int a = (int)(warp / ((long long)g.Nz * g.Ny));
     const long long rl = warp - (long long)a * g.Nz * g.Ny;
     const float* row = f + (size_t)cl.c[a] * g.Nx * g.Ny * g.Nz + (size_t)rl * g.Nx;
+    const GBuf<const float> F{f, 6LL * g.Nx * g.Ny * g.Nz};
     double re = 0.0, im = 0.0;
     for (int i = lane; i < g.Nx; i += 32) {
-        const double v = (double)row[i];
-        const double2 w = wx[i];
+        const double v = (double)F.at(row, i);
+        const double2 w = wx[PSATD_IX(i, g.Nx)];
         re += w.x * v;
         im += w.y * v;
     }
@@ -140,7 +142,7 @@ __global__ void contract_x_real_kernel(const float* __restrict__ f, GridGeom g, 
         re += __shfl_down_sync(0xffffffffu, re, o);
         im += __shfl_down_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) out[warp] = make_double2(re, im);
+    if (lane == 0) out[PSATD_IX(warp, rows)] = make_double2(re, im);
 }
 
 // Half spectrum of real fields (slots p < Nx/2 holding x mode mode[p], the x
@@ -166,15 +168,16 @@ __global__ void contract_x_half_kernel(const float2* __restrict__ S, const float
     const size_t cbase = (size_t)cl.c[a] * g.Nz * g.Ny;
     const float2* row = S + (cbase + (size_t)l * g.Ny + j) * nh;
     const float2* rowm = S + (cbase + (size_t)lm * g.Ny + jm) * nh;
+    const GBuf<const float2> SF{S, 6LL * g.Nz * g.Ny * nh};
     double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
     for (int p = lane; p < nh; p += 32) {
-        const int m = mode[p];
-        const double2 w = wx[m];
-        const float2 v = row[p];
+        const int m = mode[PSATD_IX(p, nh)];
+        const double2 w = wx[PSATD_IX(m, g.Nx)];
+        const float2 v = SF.at(row, p);
         ar += w.x * v.x - w.y * v.y;
         ai += w.x * v.y + w.y * v.x;
         if (m != 0) {
-            const float2 u = rowm[p];
+            const float2 u = SF.at(rowm, p);
             br += w.x * u.x - w.y * u.y;
             bi += w.x * u.y + w.y * u.x;
         }
@@ -186,11 +189,11 @@ __global__ void contract_x_half_kernel(const float2* __restrict__ S, const float
         bi += __shfl_down_sync(0xffffffffu, bi, o);
     }
     if (lane == 0) {
-        const double2 w = wx[nh];
-        const float2 q = Q[cbase + (size_t)l * g.Ny + j];
+        const double2 w = wx[PSATD_IX(nh, g.Nx)];
+        const float2 q = Q[PSATD_IX(cbase + (size_t)l * g.Ny + j, 6LL * g.Nz * g.Ny)];
         ar += w.x * q.x - w.y * q.y;
         ai += w.x * q.y + w.y * q.x;
-        out[warp] = make_double2(ar + br, ai - bi);
+        out[PSATD_IX(warp, rows)] = make_double2(ar + br, ai - bi);
     }
 }
 
@@ -204,12 +207,13 @@ __global__ void contract_y_kernel(const double2* __restrict__ gin, GridGeom g, i
     const double2* gr = gin + (size_t)al * g.Ny;
     const double2* w = wy + (size_t)p * g.Ny;
     double re = 0.0, im = 0.0;
+    const GBuf<const double2> Gi{gin, (long long)ncomp * g.Nz * g.Ny}, Wy{wy, (long long)ny * g.Ny};
     for (int j = 0; j < g.Ny; ++j) {
-        const double2 a = gr[j], b = w[j];
+        const double2 a = Gi.at(gr, j), b = Wy.at(w, j);
         re += b.x * a.x - b.y * a.y;
         im += b.x * a.y + b.y * a.x;
     }
-    h[tid] = make_double2(re, im);
+    h[PSATD_IX(tid, (long long)ncomp * g.Nz * ny)] = make_double2(re, im);
 }
 
 // out[a][q][p] = I_S(x_p, y_p, z_q, t) * sum_l wz[q][l] h[a][l][p]
@@ -227,15 +231,16 @@ __global__ void contract_z_kernel(const double2* __restrict__ h, GridGeom g, She
     const double2* w = wz + (size_t)q * g.Nz;
     const double2* hc = h + (size_t)a * g.Nz * ny + p;
     double re = 0.0, im = 0.0;
+    const GBuf<const double2> Hb{h, (long long)ncomp * g.Nz * ny}, Wz{wz, (long long)nz * g.Nz};
     for (int l = 0; l < g.Nz; ++l) {
-        const double2 v = hc[(size_t)l * ny], b = w[l];
+        const double2 v = Hb.at(hc, (long long)l * ny), b = Wz.at(w, l);
         re += b.x * v.x - b.y * v.y;
         im += b.x * v.y + b.y * v.x;
     }
     const double y = y0 + (y1 - y0) * p / ny;
     const double z = z0 + (z1 - z0) * q / nz;
     const double m = cut_out_indicator(x_phys, y, z, t, sh, g.c);
-    out[tid] = mk<T>((T)(re * m), (T)(im * m));
+    out[PSATD_IX(tid, (long long)ncomp * nz * ny)] = mk<T>((T)(re * m), (T)(im * m));
 }
 
 }  // namespace

@@ -36,6 +36,7 @@ EXPORTS = (
     "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile", "psatd_fp64_fma_probe",
     "psatd_multi_advance", "psatd_multi_autotune", "psatd_selftest_grid_barrier_timeout",
     "psatd_debug_set_alloc_limit", "psatd_debug_alloc_live", "psatd_debug_inject_cuda_error",
+    "psatd_debug_bounds_report",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -130,6 +131,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_debug_set_alloc_limit": (None, [C.c_longlong]),
         "psatd_debug_alloc_live": (C.c_longlong, []),
         "psatd_debug_inject_cuda_error": (None, [C.c_int, C.c_int]),
+        "psatd_debug_bounds_report": (C.c_longlong, [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
                                       C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }
