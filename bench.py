@@ -510,6 +510,27 @@ def gemm_measure(dev, stream, n=8192, reps=5):
     out["square"]["roofline"] = {"bound": "tensor", "achieved": out["square"]["tflops"], "peak": peak,
                                  "unit": "TFLOP/s", "frac": out["square"]["tflops"] / peak if peak else None,
                                  "peak_source": "measured burst bf16 (MEASURED_PEAKS.json bf16_tflops)"}
+    # bf16 operands in memory, fed by tensor copies (psatd_gemm_bf16_tma): C = A B^T
+    with torch.cuda.stream(stream):
+        A = torch.randn(n, n, device=dev).to(torch.bfloat16)
+        B = torch.randn(n, n, device=dev).to(torch.bfloat16)
+        C = torch.empty(n, n, device=dev)
+        for _ in range(2):
+            psatd.gemm_bf16_tma(A, B, C, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            psatd.gemm_bf16_tma(A, B, C, stream=stream)
+        e1.record(stream)
+        psatd.gemm_synchronize(stream)
+        ms = e0.elapsed_time(e1) / reps
+        tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+        ref = A[:256].double() @ B[:256].double().t()
+        err = float((C[:256, :256].double() - ref).abs().max() / n ** 0.5)
+        out["square_bf16_tma"] = {"shape": [n, n, n], "ms": ms, "tflops": tf, "max_abs_err_over_sqrtK": err,
+                                  "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                               "frac": tf / peak if peak else None,
+                                               "peak_source": "measured burst bf16 (MEASURED_PEAKS.json bf16_tflops)"}}
+        del A, B, C
     return out
 
 

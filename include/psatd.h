@@ -418,6 +418,19 @@ psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm,
                              long long sBk, long long sBn, float* C, long long sCm, long long sCn, float alpha,
                              float beta, int ksplit, void* cuda_stream);
 
+/* Tensor-core GEMM with bfloat16 operands in memory (the surrogate's dense
+ * contractions at scale; the paper has none): C = A B^T, A (M x K) and B (N x K)
+ * row-major bfloat16 (K contiguous), C (M x N) row-major float32, float32
+ * accumulation in tensor memory.  Operands reach shared memory through tensor
+ * copies with 128-byte swizzle, four stages deep; tiles 128 x 256.  M must be a
+ * multiple of 128, N of 256, K of 64, and the three device pointers 16-byte
+ * aligned (PSATD_ERR_ARG otherwise).  Asynchronous on cuda_stream. */
+psatd_status psatd_gemm_bf16_tma(int M, int N, int K, const void* A, const void* B, float* C, void* cuda_stream);
+
+/* Synchronise cuda_stream; PSATD_ERR_TIMEOUT if a bounded wait inside a GEMM
+ * kernel expired since the last check (the results of that GEMM are invalid). */
+psatd_status psatd_gemm_synchronize(void* cuda_stream);
+
 /* Float64 arithmetic rate probe, the denominator of the float64 solver's
  * roofline (that path is bound by float64 arithmetic, not by memory): launches
  * blocks x threads threads on cuda_stream; each runs eight independent chains

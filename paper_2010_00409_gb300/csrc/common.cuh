@@ -379,6 +379,12 @@ struct GemmArgs {
     int ksplit;
 };
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s);
+
+// C (M x N, row-major float32) = A B^T with A (M x K) and B (N x K) K-major
+// bfloat16 in device memory, fed to the tensor cores by tensor copies; M a
+// multiple of 128, N of 256, K of 64, 16-byte aligned pointers
+// (cudaErrorInvalidValue otherwise).
+cudaError_t launch_gemm_tma(const void* A, const void* B, float* C, int M, int N, int K, cudaStream_t s);
 bool gemm_take_error();
 
 }  // namespace psatd

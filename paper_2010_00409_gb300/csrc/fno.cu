@@ -636,6 +636,18 @@ psatd_status psatd_gemm_bf16(int M, int N, int K, const float* A, long long sAm,
     return launch_gemm(g, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? PSATD_OK : PSATD_ERR_CUDA;
 }
 
+psatd_status psatd_gemm_bf16_tma(int M, int N, int K, const void* A, const void* B, float* C, void* cuda_stream) {
+    if (!A || !B || !C) return PSATD_ERR_ARG;
+    const cudaError_t e = launch_gemm_tma(A, B, C, M, N, K, static_cast<cudaStream_t>(cuda_stream));
+    if (e == cudaErrorInvalidValue) return PSATD_ERR_ARG;
+    return e == cudaSuccess ? PSATD_OK : PSATD_ERR_CUDA;
+}
+
+psatd_status psatd_gemm_synchronize(void* cuda_stream) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return PSATD_ERR_CUDA;
+    return gemm_take_error() ? PSATD_ERR_TIMEOUT : PSATD_OK;
+}
+
 psatd_status psatd_fno_synchronize(psatd_fno* f) {
     if (!f) return PSATD_ERR_ARG;
     FCK(cudaStreamSynchronize(f->stream));

@@ -9,6 +9,7 @@
 // tiles to C with float atomics (C must hold beta * C beforehand; the launcher
 // scales it).
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 
@@ -289,6 +290,190 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(GemmArgs g, int ntm
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// bf16 operands in memory, fed by the tensor copy engine: C = A B^T with A (M x
+// K) and B (N x K) both K-major bf16, C (M x N) row-major float32.  Tile 128 x
+// 256, K in blocks of 64 (128 bytes of bf16 per row, one 128-byte swizzle
+// atom), four stages of 48 KB.  Warp 0 (one lane) issues the tensor copies of
+// a stage once the MMAs have released it; warp 1 (one lane) issues the four
+// K = 16 MMAs of each stage into one of two accumulators of 256 columns in
+// tensor memory and commits the stage back to the producer and, after a tile's
+// last stage, the accumulator to the epilogue; warps 2-5 read the accumulator
+// (warp w reads lanes 32 (w % 4) .. + 31, i.e. rows of its quarter) and store
+// the rows, then hand the accumulator back.  Tiles are visited in groups of 16
+// along M so that the tiles in flight share operand rows in L2.
+//
+// Shared-memory operands are in the canonical K-major 128-byte-swizzle layout
+// that the copy engine writes with CU_TENSOR_MAP_SWIZZLE_128B: row r of a
+// block at r * 128 bytes, 8-row atoms of 1024 bytes (the descriptor's stride
+// offset), 16-byte chunks permuted within a row by the copy engine; the K = 16
+// steps inside the atom advance the descriptor's start address by 32 bytes.
+constexpr int GT_BM = 128, GT_BN = 256, GT_BK = 64, GT_STAGES = 4, GT_THREADS = 192, GT_GROUP_M = 16;
+constexpr int GT_STAGE_A = GT_BM * GT_BK * 2, GT_STAGE_B = GT_BN * GT_BK * 2;
+constexpr int GT_STAGE = GT_STAGE_A + GT_STAGE_B;
+constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;           // + alignment slack
+constexpr int GT_TMEM_COLS = 2 * GT_BN;
+
+__device__ __forceinline__ uint64_t gt_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);                       // version 1, 128-byte swizzle
+}
+
+__device__ __forceinline__ void gt_arrive_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void gt_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(bar)) : "memory");
+}
+
+__device__ __forceinline__ void gt_load(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(tc_smem(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(tc_smem(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void gt_tile(int tile, int ntm, int ntn, int* mt, int* nt) {
+    const int per_group = GT_GROUP_M * ntn;
+    const int gi = tile / per_group, in = tile - gi * per_group;
+    const int m_first = gi * GT_GROUP_M;
+    const int gm = min(GT_GROUP_M, ntm - m_first);
+    *mt = m_first + in % gm;
+    *nt = in / gm;
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 1)
+gemm_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                float* __restrict__ C, int M, int N, int K, int ntm, int ntn) {
+    extern __shared__ __align__(1024) unsigned char gt_raw[];
+    __shared__ __align__(8) uint64_t full[GT_STAGES], empty[GT_STAGES], afull[2], aempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int any_err;
+    unsigned char* smem = gt_raw + ((1024 - (tc_smem(gt_raw) & 1023)) & 1023);   // 1024-byte aligned stages
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = ntm * ntn, nkb = K / GT_BK;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_base)),
+                     "r"(GT_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < GT_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&full[i])), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&empty[i])), "r"(1) : "memory");
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&afull[i])), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&aempty[i])), "r"(4) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        any_err = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {                                   // producer: tensor copies
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                int mt, nt;
+                gt_tile(tile, ntm, ntn, &mt, &nt);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % GT_STAGES;
+                    ok = tc_wait(&empty[s], ((it / GT_STAGES) & 1) ^ 1) && ok;
+                    unsigned char* sa = smem + s * GT_STAGE;
+                    gt_arrive_expect(&full[s], GT_STAGE);
+                    gt_load(sa, &map_a, &full[s], kb * GT_BK, mt * GT_BM);
+                    gt_load(sa + GT_STAGE_A, &map_b, &full[s], kb * GT_BK, nt * GT_BN);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                   // MMA issue
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GT_BN >> 3) << 17) |
+                                       ((uint32_t)(GT_BM >> 4) << 24);
+            uint32_t it = 0, tl = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+                const int acc = tl & 1;
+                ok = tc_wait(&aempty[acc], ((tl >> 1) & 1) ^ 1) && ok;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + acc * GT_BN;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % GT_STAGES;
+                    ok = tc_wait(&full[s], (it / GT_STAGES) & 1) && ok;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = tc_smem(smem + s * GT_STAGE), sb = sa + GT_STAGE_A;
+#pragma unroll
+                    for (int kk = 0; kk < GT_BK / 16; ++kk) {
+                        const uint64_t ad = gt_desc(sa + kk * 32), bd = gt_desc(sb + kk * 32);
+                        const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                                     : "memory");
+                    }
+                    tc_commit(&empty[s]);                  // the stage is free once these MMAs have read it
+                }
+                tc_commit(&afull[acc]);                    // the tile's accumulator is complete
+            }
+        }
+    } else {                                               // epilogue: warps 2-5
+        const int q = warp & 3;
+        uint32_t tl = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+            int mt, nt;
+            gt_tile(tile, ntm, ntn, &mt, &nt);
+            const int acc = tl & 1;
+            ok = tc_wait(&afull[acc], (tl >> 1) & 1) && ok;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m = mt * GT_BM + 32 * q + lane;
+            float* row = C + (size_t)m * N + (size_t)nt * GT_BN;
+            const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + acc * GT_BN;
+#pragma unroll 1
+            for (int c = 0; c < GT_BN; c += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(base + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float4* dst = reinterpret_cast<float4*>(row + c);
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                         __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) gt_arrive(&aempty[acc]);        // the MMAs may write this accumulator again
+        }
+    }
+    if (!ok) {
+        atomicExch(&g_gemm_error, 1);
+        any_err = 1;
+    }
+    __syncthreads();
+    if (any_err && threadIdx.x == 0) {
+        // an expired wait left the pipeline out of step: second bounded waits so
+        // that no copy or MMA is still in flight when the block leaves
+        for (int i = 0; i < 2; ++i) tc_wait(&afull[i], 0), tc_wait(&afull[i], 1);
+        for (int i = 0; i < GT_STAGES; ++i) tc_wait(&full[i], 0), tc_wait(&full[i], 1);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_TMEM_COLS)
+                     : "memory");
+}
+
 __global__ void scale_kernel(GemmArgs g) {
     const long long total = (long long)g.nb0 * g.nb1 * g.M * g.N;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -355,6 +540,62 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s) {
         k<<<(unsigned)grid, kTcThreads, smem_launch[bi], s>>>(g, (int)ntm, (int)ntn, (int)ntiles);
         return cudaGetLastError();
     }
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 gemm_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2D map of a K-major bf16 matrix (rows x K), box 64 (K) x box_rows, 128-byte swizzle
+bool gemm_map(CUtensorMap* map, const void* ptr, int rows, int K, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = gemm_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)GT_BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+cudaError_t launch_gemm_tma(const void* A, const void* B, float* C, int M, int N, int K, cudaStream_t s) {
+    if (M % GT_BM || N % GT_BN || K % GT_BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15)
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!gemm_map(&ma, A, M, K, GT_BM) || !gemm_map(&mb, B, N, K, GT_BN)) return cudaErrorInvalidValue;
+    static int sms = 0;
+    static bool attr = false;
+    if (!attr) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+        const cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   GT_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntm = M / GT_BM, ntn = N / GT_BN;
+    const long long ntiles = (long long)ntm * ntn;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    gemm_tma_kernel<<<grid, GT_THREADS, GT_SMEM, s>>>(ma, mb, C, M, N, K, ntm, ntn);
+    return cudaGetLastError();
 }
 
 // Read and clear the flag of an expired bounded wait in the GEMM kernel

@@ -36,7 +36,7 @@ EXPORTS = (
     "psatd_gemm_bf16", "psatd_set_mapping", "psatd_set_pulse_profile", "psatd_fp64_fma_probe",
     "psatd_multi_advance", "psatd_multi_autotune", "psatd_selftest_grid_barrier_timeout",
     "psatd_debug_set_alloc_limit", "psatd_debug_alloc_live", "psatd_debug_inject_cuda_error",
-    "psatd_debug_bounds_report",
+    "psatd_debug_bounds_report", "psatd_gemm_bf16_tma", "psatd_gemm_synchronize",
 )
 PATH_AUTO, PATH_GENERIC, PATH_REGISTER = 0, 1, 2
 
@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "psatd_debug_alloc_live": (C.c_longlong, []),
         "psatd_debug_inject_cuda_error": (None, [C.c_int, C.c_int]),
         "psatd_debug_bounds_report": (C.c_longlong, [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "psatd_gemm_bf16_tma": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P, P]),
+        "psatd_gemm_synchronize": (C.c_int, [P]),
         "psatd_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_longlong, C.c_longlong, P, C.c_longlong,
                                       C.c_longlong, P, C.c_longlong, C.c_longlong, C.c_float, C.c_float, C.c_int, P]),
     }
@@ -309,6 +311,27 @@ def gemm_bf16(A, B, Cout, alpha=1.0, beta=0.0, ksplit=1, stream=None):
                                alpha, beta, ksplit, C.c_void_p(s.cuda_stream))
     _check(st, None)
     return Cout
+
+
+def gemm_bf16_tma(A, B, Cout, stream=None):
+    """Cout = A @ B.T on the tensor cores: A (M x K), B (N x K) bfloat16 CUDA
+    tensors, Cout (M x N) float32, all contiguous; M % 128, N % 256, K % 64 == 0."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    M, K = A.shape
+    N = B.shape[0]
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and Cout.dtype == torch.float32
+    assert A.is_contiguous() and B.is_contiguous() and Cout.is_contiguous() and B.shape[1] == K
+    assert tuple(Cout.shape) == (M, N)
+    _check(lib().psatd_gemm_bf16_tma(M, N, K, C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                                     C.c_void_p(Cout.data_ptr()), C.c_void_p(s.cuda_stream)), None)
+    return Cout
+
+
+def gemm_synchronize(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().psatd_gemm_synchronize(C.c_void_p(s.cuda_stream)), None)
 
 
 def fp64_fma_probe(out, blocks, threads, iters, stream=None):
