@@ -57,7 +57,11 @@ template <typename V> struct GBuf {
     V* base;
     long long n;
     __device__ __forceinline__ V& at(const V* p, long long k) const {
+#ifdef PSATD_DEBUG
         return base[PSATD_IX((long long)(p - base) + k, n)];
+#else
+        return const_cast<V&>(p[k]);                 // release: exactly p[k]
+#endif
     }
     __device__ __forceinline__ V& operator[](long long i) const { return base[PSATD_IX(i, n)]; }
 };

@@ -63,8 +63,9 @@ __device__ __forceinline__ void group_sync(int h) {
 // field tiles take its tiles of W k_y values (copied through map_nyq, a 3D map
 // {Ny, Nz, 6}).  SPECTRAL_OUT with HALF leaves the updated half spectrum (slots
 // and the Nyquist array) in natural k_z order.
-template <typename T, int N1, int N2, int W, int G, bool SPECTRAL_OUT, bool HALF>
-__global__ void __launch_bounds__(W * N2 * G)
+// float32: two blocks per SM (128 registers a thread, the 96 KB tile twice)
+template <typename T, int N1, int N2, int W, int G, bool SPECTRAL_OUT, bool HALF, bool PROJ = false>
+__global__ void __launch_bounds__(W * N2 * G, sizeof(T) == 4 ? 2 : 1)
 kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_nyq,
                   cplx<T>* __restrict__ data, int Nx, int Ny, const cplx<T>* __restrict__ tw,
                   const T* __restrict__ kxs, const T* __restrict__ kys, const T* __restrict__ kzs,
@@ -226,10 +227,12 @@ kspace_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant
         const ModeCoef<T> mm = mc[m];
         if constexpr (HALF) {
             const bool fz = ((j + N2 * (r / N2)) + N1 * (r % N2)) == Nz / 2;
-            if (project_e)
-                project_b_mean<T>(Ex, Ey, Ez, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
-            if (project_b)
-                project_b_mean<T>(Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
+            if constexpr (PROJ) {                       // (the step's instance carries no projection)
+                if (project_e)
+                    project_b_mean<T>(Ex, Ey, Ez, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
+                if (project_b)
+                    project_b_mean<T>(Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq, 2 * y == Ny, fz);
+            }
             rotate_mode_mean<T>(Ex, Ey, Ez, Bx, By, Bz, kx * mm.kinv, ky * mm.kinv, kzr[m] * mm.kinv, nq,
                                 2 * y == Ny, fz, mm.C, mm.S);
         } else {
@@ -321,8 +324,10 @@ cudaError_t kspace_tma_launch(const CUtensorMap& map, cplx<T>* data, const GridG
                               int* err, cudaStream_t s, bool spectral_out, bool project_b, const HalfSlots<T>* half) {
     constexpr int G = 2;
     const size_t smem = (size_t)6 * N1 * N2 * W * sizeof(cplx<T>);
-    auto k = half ? (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, true>
-                                  : kspace_tma_kernel<T, N1, N2, W, G, false, true>)
+    const bool proj = half && (project_b || half->project_e);
+    auto k = half ? (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, true, true>
+                                  : (proj ? kspace_tma_kernel<T, N1, N2, W, G, false, true, true>
+                                          : kspace_tma_kernel<T, N1, N2, W, G, false, true, false>))
                   : (spectral_out ? kspace_tma_kernel<T, N1, N2, W, G, true, false>
                                   : kspace_tma_kernel<T, N1, N2, W, G, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
