@@ -97,8 +97,11 @@ def dist_env():
 # step kernel kind, from one ncu capture at 256^3 (the plane kernels: mean of
 # the forward and inverse launches), keyed by (kernel, size, storage); to be
 # re-taken whenever that kernel changes.
-NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.69e6, ("plane_xy", 256, "real"): 750.11e6,
-                     ("kspace_z", 256, "complex"): 1621.73e6, ("kspace_z", 256, "real"): 822.44e6}
+NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.69e6, ("plane_xy", 256, "real"): 750.26e6,
+                     ("kspace_z", 256, "complex"): 1621.73e6, ("kspace_z", 256, "real"): 824.13e6}
+# Where each figure above was captured (profiles/ summaries, one full-set launch each).
+NCU_TRAFFIC_SOURCE = {"complex": "profiles/psatd_step_tight_focus_256.md",
+                      "real": "profiles/psatd_real_step_tight_focus_256.md"}
 
 
 def measured_peaks():
@@ -574,7 +577,9 @@ def step_roofline(prof, g, storage, size, peak, peak_src):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
             if peak_src == "measured" else "fallback 6.8 TB/s",
-            "traffic": NCU_TRAFFIC_BYTES.get((dom, size, storage)), "bytes_per_launch": bytes_per_launch,
+            "traffic": NCU_TRAFFIC_BYTES.get((dom, size, storage)),
+            "traffic_source": NCU_TRAFFIC_SOURCE[storage] if (dom, size, storage) in NCU_TRAFFIC_BYTES else None,
+            "bytes_per_launch": bytes_per_launch,
             "bytes_per_cell_per_launch": B, "avg_launch_ms": dom_ms / dom_n, "launches": dom_n}
     hbm = {"algorithmic_bytes_per_cell_step": sweep_bytes / n_st / g.cells,
            "achieved_GBps": sweep_bytes / (step_total / 1e3) / 1e9,

@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc_kernel(GemmArgs g, int ntm
 // block at r * 128 bytes, 8-row atoms of 1024 bytes (the descriptor's stride
 // offset), 16-byte chunks permuted within a row by the copy engine; the K = 16
 // steps inside the atom advance the descriptor's start address by 32 bytes.
-constexpr int GT_BM = 128, GT_BN = 256, GT_BK = 64, GT_STAGES = 4, GT_THREADS = 192, GT_GROUP_M = 16;
+#ifndef PSATD_GT_GROUP_M
+#define PSATD_GT_GROUP_M 16
+#endif
+constexpr int GT_BM = 128, GT_BN = 256, GT_BK = 64, GT_STAGES = 4, GT_THREADS = 192, GT_GROUP_M = PSATD_GT_GROUP_M;
 constexpr int GT_STAGE_A = GT_BM * GT_BK * 2, GT_STAGE_B = GT_BN * GT_BK * 2;
 constexpr int GT_STAGE = GT_STAGE_A + GT_STAGE_B;
 constexpr int GT_SMEM = GT_STAGES * GT_STAGE + 1024;           // + alignment slack
