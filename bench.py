@@ -97,8 +97,8 @@ def dist_env():
 # step kernel kind, from one ncu capture at 256^3 (the plane kernels: mean of
 # the forward and inverse launches), keyed by (kernel, size, storage); to be
 # re-taken whenever that kernel changes.
-NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.69e6, ("plane_xy", 256, "real"): 750.26e6,
-                     ("kspace_z", 256, "complex"): 1621.73e6, ("kspace_z", 256, "real"): 824.13e6}
+NCU_TRAFFIC_BYTES = {("plane_xy", 256, "complex"): 1549.25e6, ("plane_xy", 256, "real"): 749.62e6,
+                     ("kspace_z", 256, "complex"): 1627.90e6, ("kspace_z", 256, "real"): 824.13e6}
 # Where each figure above was captured (profiles/ summaries, one full-set launch each).
 NCU_TRAFFIC_SOURCE = {"complex": "profiles/psatd_step_tight_focus_256.md",
                       "real": "profiles/psatd_real_step_tight_focus_256.md"}
