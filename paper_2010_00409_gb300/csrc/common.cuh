@@ -199,6 +199,7 @@ struct PulseParams {
 // Device tables of one context.
 template <typename T> struct Tables {
     const cplx<T>* tw[3];       // tw[a][t] = exp(-2 pi i t / N_a), t < N_a
+    const cplx<T>* tw_x2 = nullptr;   // [32][32] tw[0][(a b) mod N_x] (N_x = 512, 1024): the row-fused pass
     const T* k[3];              // k_a[i] = 2 pi m(i) / (N_a d_a)
     const ModeCoef<T>* coef;    // (Nz/2+1) x (Ny/2+1) x (Nx/2+1)
     AxisPlan plan[3];
@@ -261,6 +262,14 @@ cudaError_t launch_fft_axis_fast(cplx<T>* data, int ncomp, const GridGeom& g, co
                                  int axis, int dir, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kspace_fast(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
+
+// Fused x pass of a step in z, y, x order (N_x = 512 or 1024 in float32,
+// complex storage): forward x, the Eq. 3-4 update of every mode, inverse x, one
+// block per (k_y, k_z) row with all six components; y and z already in k-space.
+// cudaErrorNotSupported (nothing launched) for other shapes.
+template <typename T>
+cudaError_t launch_kspace_rows(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s);
+bool kspace_rows_supported(int prec, const GridGeom& g);
 
 // Half spectrum of real fields in the slot order of the real-field plane
 // kernels: per slot p < Nx/2 the wave number k_x, and the coefficient table

@@ -32,8 +32,11 @@ template <typename T, int N1, int N2> struct RowsCfg {
 // along y (rows one plane row apart), 128 KB along z, whose rows lie a whole
 // plane apart (at 1024^2 planes, 32-byte runs 8 MB apart used the DRAM bursts
 // poorly: the z transforms took 2.3 times as long as with 128-byte runs)
+#ifndef PSATD_COLS_Y_BUDGET
+#define PSATD_COLS_Y_BUDGET (48 * 1024)
+#endif
 template <typename T, int N, bool ZAXIS> constexpr int cols_width() {
-    const int budget = ZAXIS ? 128 * 1024 : 48 * 1024;
+    const int budget = ZAXIS ? 128 * 1024 : PSATD_COLS_Y_BUDGET;
     int w = 128 / (int)sizeof(cplx<T>);
     while (w > 1 && N * w * (int)sizeof(cplx<T>) > budget) w /= 2;
     return w;

@@ -97,6 +97,7 @@ struct psatd_ctx {
     DevBuf slot_mode;                   // real fields: x mode index per slot (sampling from the half spectrum)
     DevBuf slot_coef_proj;              // real fields: projection table (C = 1/Ntot, S = 0) in slot order
     DevBuf nyq;                         // real fields: x Nyquist spectrum [6][Nz][Ny] between the plane kernels
+    DevBuf tw_x2;                       // N_x = 512 / 1024: [32][32] x twiddles of the row-fused k-space pass
     CUtensorMap nyq_map;                // ... and its tensor map for the k-space kernel (128-B aligned type)
     bool nyq_map_ok = false;
 
@@ -272,6 +273,7 @@ Tables<T> tables(const psatd_ctx* c) {
         tb.plan[a] = c->plan[a];
     }
     tb.coef = static_cast<const ModeCoef<T>*>(c->coef.p);
+    tb.tw_x2 = static_cast<const cplx<T>*>(c->tw_x2.p);
     return tb;
 }
 
@@ -302,6 +304,14 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
         CK(c, ensure_buf(c->k[a], N * sizeof(T)));
         CK(c, cudaMemcpy(c->tw[a].p, tw.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice));
         CK(c, cudaMemcpy(c->k[a].p, k.data(), N * sizeof(T), cudaMemcpyHostToDevice));
+        if (a == 0 && (N == 512 || N == 1024)) {
+            // the row-fused pass reads W^{a b} for a, b < 32 along a thread-indexed b
+            std::vector<cplx<T>> t2(32 * 32);
+            for (int i = 0; i < 32; ++i)
+                for (int j = 0; j < 32; ++j) t2[i * 32 + j] = tw[(i * j) % N];
+            CK(c, ensure_buf(c->tw_x2, t2.size() * sizeof(cplx<T>)));
+            CK(c, cudaMemcpy(c->tw_x2.p, t2.data(), t2.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+        }
     }
     return PSATD_OK;
 }
@@ -543,7 +553,22 @@ cudaError_t spectral_pass(psatd_ctx* c, int mode, double scale) {
     const GridGeom g = geom(c);
     const Tables<T> tb = tables<T>(c);
     cplx<T>* f = static_cast<cplx<T>*>(c->fields);
-    cudaError_t e = plane_xy<T>(c, f, 6, -1, -1);
+    cudaError_t e;
+    if (mode == KS_ROTATE && c->kernel_path == PSATD_PATH_AUTO && kspace_rows_supported(c->prec, g) &&
+        !(g.Nz == 64 || g.Nz == 128 || g.Nz == 256)) {
+        // no fused z pass for this N_z: forward z, y; the update fused into the
+        // x pass (forward x, update, inverse x in one launch); inverse y, z
+        if ((e = fft_axis<T>(c, f, 6, 2, -1, -1)) != cudaSuccess) return e;
+        if ((e = fft_axis<T>(c, f, 6, 1, -1, -1)) != cudaSuccess) return e;
+        e = timed(c, PSATD_KERNEL_KSPACE, [&] {
+            ++c->launches;
+            return launch_kspace_rows<T>(f, g, tb, c->stream);
+        });
+        if (e != cudaSuccess) return e;
+        if ((e = fft_axis<T>(c, f, 6, 1, +1, -1)) != cudaSuccess) return e;
+        return fft_axis<T>(c, f, 6, 2, +1, -1);
+    }
+    e = plane_xy<T>(c, f, 6, -1, -1);
     const bool fused_xy = (e == cudaSuccess);
     if (!fused_xy) {
         if (e != cudaErrorNotSupported) return e;
@@ -1023,7 +1048,7 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef_T);
     free_buf(c->coef_proj);
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
-    free_buf(c->slot_mode); free_buf(c->slot_coef_proj);
+    free_buf(c->slot_mode); free_buf(c->slot_coef_proj); free_buf(c->tw_x2);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->lprof);
     free_buf(c->multi);

@@ -328,6 +328,25 @@ def test_fast_kernels_match_oracle_and_generic(lib, prec, shape):
     assert rel(out[lib.PATH_REGISTER][1], out[lib.PATH_GENERIC][1]) <= 2 * TOL[prec]
 
 
+# x lengths 512 / 1024 in float32 with a z length that has no fused z kernel:
+# the step takes z, y, then the x pass with the update fused into it, then y, z.
+@pytest.mark.parametrize("shape", [(1024, 6, 36), (512, 10, 300), (1024, 1, 2), (1024, 16, 1), (512, 3, 5)])
+def test_row_fused_kspace_step_matches_oracle(lib, shape):
+    Nx, Ny, Nz = shape
+    g = W.GridSpec(Nx, Ny, Nz, 0.5, 0.7, 0.3, 0.0, 0.0, 0.0, 1.0)
+    f = W.random_complex_field((6, Nz, Ny, Nx), seed=Nx + 5 * Ny + Nz)
+    dt = 0.37
+    with lib.Context(g, None, dt, 32) as ctx:
+        ctx.set_fields(f)
+        ctx.profile_enable(True)
+        ctx.advance(3)
+        prof = ctx.profile_read()
+        got = ctx.get_field(-1)
+    assert prof["kspace_z"][1] == 3                     # one fused launch per step
+    assert "plane_xy" not in prof and prof.get("fft_x", (0, 0))[1] == 0
+    assert rel(got, O.advance(f, ogrid(g), dt, 3)) <= 3 * TOL[32]
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(lib):
     import ctypes as C
     g = W.plain_grid(64)
