@@ -199,7 +199,9 @@ struct PulseParams {
 // Device tables of one context.
 template <typename T> struct Tables {
     const cplx<T>* tw[3];       // tw[a][t] = exp(-2 pi i t / N_a), t < N_a
-    const cplx<T>* tw_x2 = nullptr;   // [32][32] tw[0][(a b) mod N_x] (N_x = 512, 1024): the row-fused pass
+    // [32][32] tw[a][(i j) mod N_a] for N_a = 512, 1024 (else null): twiddles of
+    // the register kernels read along a thread-indexed j, 32 consecutive entries
+    const cplx<T>* tw2[3] = {nullptr, nullptr, nullptr};
     const T* k[3];              // k_a[i] = 2 pi m(i) / (N_a d_a)
     const ModeCoef<T>* coef;    // (Nz/2+1) x (Ny/2+1) x (Nx/2+1)
     AxisPlan plan[3];

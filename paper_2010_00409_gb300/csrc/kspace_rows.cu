@@ -157,7 +157,7 @@ cudaError_t rows_launch(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, c
     if (e != cudaSuccess) return e;
     const long long blocks = (long long)g.Ny * g.Nz;
     if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
-    k<<<(unsigned)blocks, 6 * N2, smem, s>>>(data, g.Ny, g.Nz, tb.tw_x2, tb.k[0], tb.k[1], tb.k[2], tb.coef);
+    k<<<(unsigned)blocks, 6 * N2, smem, s>>>(data, g.Ny, g.Nz, tb.tw2[0], tb.k[0], tb.k[1], tb.k[2], tb.coef);
     return cudaGetLastError();
 }
 
@@ -172,7 +172,7 @@ bool kspace_rows_supported(int prec, const GridGeom& g) {
 // already be in k-space), or cudaErrorNotSupported (nothing launched).
 template <typename T>
 cudaError_t launch_kspace_rows(cplx<T>* data, const GridGeom& g, const Tables<T>& tb, cudaStream_t s) {
-    if (!tb.tw_x2) return cudaErrorNotSupported;
+    if (!tb.tw2[0]) return cudaErrorNotSupported;
     if constexpr (sizeof(T) == 4) {
         if (g.Nx == 1024) return rows_launch<T, 32, 32>(data, g, tb, s);
         if (g.Nx == 512) return rows_launch<T, 32, 16>(data, g, tb, s);

@@ -97,7 +97,7 @@ struct psatd_ctx {
     DevBuf slot_mode;                   // real fields: x mode index per slot (sampling from the half spectrum)
     DevBuf slot_coef_proj;              // real fields: projection table (C = 1/Ntot, S = 0) in slot order
     DevBuf nyq;                         // real fields: x Nyquist spectrum [6][Nz][Ny] between the plane kernels
-    DevBuf tw_x2;                       // N_x = 512 / 1024: [32][32] x twiddles of the row-fused k-space pass
+    DevBuf tw2[3];                      // N_a = 512 / 1024: [32][32] twiddles of the register kernels
     CUtensorMap nyq_map;                // ... and its tensor map for the k-space kernel (128-B aligned type)
     bool nyq_map_ok = false;
 
@@ -273,7 +273,7 @@ Tables<T> tables(const psatd_ctx* c) {
         tb.plan[a] = c->plan[a];
     }
     tb.coef = static_cast<const ModeCoef<T>*>(c->coef.p);
-    tb.tw_x2 = static_cast<const cplx<T>*>(c->tw_x2.p);
+    for (int a = 0; a < 3; ++a) tb.tw2[a] = static_cast<const cplx<T>*>(c->tw2[a].p);
     return tb;
 }
 
@@ -304,13 +304,15 @@ psatd_status upload_axis_tables(psatd_ctx* c) {
         CK(c, ensure_buf(c->k[a], N * sizeof(T)));
         CK(c, cudaMemcpy(c->tw[a].p, tw.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice));
         CK(c, cudaMemcpy(c->k[a].p, k.data(), N * sizeof(T), cudaMemcpyHostToDevice));
-        if (a == 0 && (N == 512 || N == 1024)) {
-            // the row-fused pass reads W^{a b} for a, b < 32 along a thread-indexed b
+        if (N == 512 || N == 1024) {
+            // the register kernels read W^{i j} for i, j < 32 along a thread-indexed j
             std::vector<cplx<T>> t2(32 * 32);
             for (int i = 0; i < 32; ++i)
                 for (int j = 0; j < 32; ++j) t2[i * 32 + j] = tw[(i * j) % N];
-            CK(c, ensure_buf(c->tw_x2, t2.size() * sizeof(cplx<T>)));
-            CK(c, cudaMemcpy(c->tw_x2.p, t2.data(), t2.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+            CK(c, ensure_buf(c->tw2[a], t2.size() * sizeof(cplx<T>)));
+            CK(c, cudaMemcpy(c->tw2[a].p, t2.data(), t2.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+        } else {
+            free_buf(c->tw2[a]);
         }
     }
     return PSATD_OK;
@@ -1048,7 +1050,8 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef_T);
     free_buf(c->coef_proj);
     free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
-    free_buf(c->slot_mode); free_buf(c->slot_coef_proj); free_buf(c->tw_x2);
+    free_buf(c->slot_mode); free_buf(c->slot_coef_proj);
+    for (int a = 0; a < 3; ++a) free_buf(c->tw2[a]);
     free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
     free_buf(c->lprof);
     free_buf(c->multi);

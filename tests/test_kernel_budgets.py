@@ -1,8 +1,9 @@
 """Register budgets of the step kernels (CPU: nvcc -Xptxas -v, no GPU needed).
 
 The real-field step keeps four r2c / five c2r plane blocks and two k-space
-blocks per SM; a kernel that grows past its register budget loses a resident
-block and the step slows by a third, so the budgets are checked at build time.
+blocks per SM, the row-fused k-space pass four blocks; a kernel that grows past
+its register budget loses a resident block and the step slows by a third, so
+the budgets are checked at build time.
 """
 import os
 import re
@@ -22,6 +23,7 @@ BUDGETS = [
     ("kspace_tma.cu", r"kspace_tma_kernelIfLi16ELi16ELi8ELi2ELb0ELb1ELb0E", 128),   # real-field step
     ("kspace_tma.cu", r"kspace_tma_kernelIfLi16ELi16ELi8ELi2ELb0ELb0ELb0E", 128),   # complex step
     ("gemm.cu", r"gemm_tma_kernel", 64),
+    ("kspace_rows.cu", r"kspace_rows_kernelIfLi32ELi32E", 80),                     # 1024-point rows, four blocks per SM
 ]
 
 
