@@ -391,6 +391,14 @@ def multi_octave_measure(dev, stream, k=8):
         e1.record(stream)
         d1 = ctx.diagnostics()
         ms_step = e0.elapsed_time(e1) / k
+        # two more steps with per-launch events: the kernels of one step
+        n0 = ctx.launch_count
+        ctx.profile_enable(True)
+        ctx.advance(2)
+        ctx.synchronize()
+        kinds = {kk: {"ms_per_step": v[0] / 2, "launches_per_step": v[1] / 2} for kk, v in ctx.profile_read().items()}
+        ctx.profile_enable(False)
+        launches = (ctx.launch_count - n0) / 2
         if to_focus:
             stepped = ctx.sample_focal_plane(plane["x_p"], *pa, comps=(0, 1, 2))
         ctx.focal_one_shot(p, T, plane["x_p"], *pa, comps=(0, 1, 2))       # warm-up (tables for T)
@@ -408,8 +416,16 @@ def multi_octave_measure(dev, stream, k=8):
     extra = {}
     if stepped is not None:
         extra["stepped_focal_rel_l2_err_vs_fp64_768"] = float(np.linalg.norm(stepped - f64) / np.linalg.norm(f64))
+    peak, peak_src = measured_peaks()
+    path_bytes = 96.0 * launches                       # every launch of this path reads and writes the field once
+    hbm = {"graded_bytes_per_cell_step": 288, "achieved_GBps_graded": g.cells * 288 / (ms_step * 1e-3) / 1e9,
+           "frac_graded": g.cells * 288 / (ms_step * 1e-3) / 1e9 / peak,
+           "path_sweeps_per_step": launches, "path_bytes_per_cell_step": path_bytes,
+           "achieved_GBps_path": g.cells * path_bytes / (ms_step * 1e-3) / 1e9,
+           "frac_path": g.cells * path_bytes / (ms_step * 1e-3) / 1e9 / peak,
+           "peak": peak, "peak_source": peak_src, "kernels": kinds}
     return dict({"grid": [g.Nx, g.Ny, g.Nz], "precision": "fp32, complex storage", "psatd_steps": k,
-            "ms_per_psatd_step": ms_step, "cell_steps_per_s": g.cells / (ms_step * 1e-3),
+            "ms_per_psatd_step": ms_step, "cell_steps_per_s": g.cells / (ms_step * 1e-3), "hbm": hbm,
             "energy_drift": d1["energy"] / d0["energy"] - 1,
             "max_div_E_rel": d1["max_div_E"] / max(d1["max_E_hat"], 1e-300),
             "steps_to_focus": n_steps,
