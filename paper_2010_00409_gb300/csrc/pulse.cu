@@ -45,13 +45,20 @@ __device__ __forceinline__ double profile_ul(double zeta, const PulseParams& p, 
     return ar * cos(phase) - ai * sin(phase);
 }
 
+// The closed support |R - R0| <= L/2 (and R > 0) in float64.
+__device__ __forceinline__ bool edge_inside(double X, double Y, double Z, const ShellGeom& sh) {
+    const double R = sqrt(X * X + Y * Y + Z * Z);
+    if (!(R > 0.0)) return false;
+    const double zeta = R - sh.R0;
+    return !(zeta < -0.5 * sh.L || zeta > 0.5 * sh.L);
+}
+
 // Scalar amplitude u(R) with carrier phase `phase`; 0 outside the support.
 __device__ __forceinline__ double pulse_u(double X, double Y, double Z, const PulseParams& p,
                                           const ShellGeom& sh, double phase) {
+    if (!edge_inside(X, Y, Z, sh)) return 0.0;
     const double R = sqrt(X * X + Y * Y + Z * Z);
-    if (!(R > 0.0)) return 0.0;
     const double zeta = R - sh.R0;
-    if (zeta < -0.5 * sh.L || zeta > 0.5 * sh.L) return 0.0;
     const double alpha = atan2(sqrt(Y * Y + Z * Z), -X);   // angle from the -x axis
     if (p.kind == 0) {
         // flat-top, Eq. 7-8
@@ -98,59 +105,112 @@ __device__ __forceinline__ float u_ts_flat_f(float a, float th, float eps) {
     return 0.f;
 }
 
+// Double-float arithmetic: an unevaluated sum h + l of two float32 values
+// (|l| <= ulp(h) / 2), about 48 significant bits from float32 operations only
+// (exact products by fmaf, exact sums by the two-sum of Knuth), so that the
+// float32-storage initialiser needs no float64 arithmetic at all.
+struct FF {
+    float h, l;
+};
+__host__ __device__ __forceinline__ FF ff_from(double v) {
+    FF f;
+    f.h = (float)v;
+    f.l = (float)(v - (double)f.h);
+    return f;
+}
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF quick_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF two_prod(float a, float b) {
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = two_sum(a.h, b.h);
+    return quick_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const FF p = two_prod(a.h, b.h);
+    return quick_two_sum(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+    const FF p = two_prod(a.h, b);
+    return quick_two_sum(p.h, fmaf(a.l, b, p.l));
+}
+__device__ __forceinline__ FF ff_sqr(FF a) {
+    const FF p = two_prod(a.h, a.h);
+    return quick_two_sum(p.h, fmaf(2.f * a.h, a.l, p.l));
+}
+
 // Per-launch constants of the float32-storage evaluation (built on the host).
 struct PulseF32 {
-    double R0, halfL, k0, inv2pi, two_pi, phase, prof_z0, prof_inv_dz;
     double cps, sps;        // cos, sin of the polarisation angle (float64 storage)
-    float lo2, hi2, pi_over_L, th, eps, inv_th2, g4, amp, amp_R0, ell;
+    FF x0, y0, z0, dx, dy, dz, D;      // the grid
+    FF R0, k0, phase, two_pi, prof_z0, prof_inv_dz;
+    float halfL, inv2pi, lo2, hi2, pi_over_L, th, eps, inv_th2, g4, amp, amp_R0, ell;
     float cp[2], sp[2];     // cos, sin of the carrier phases cep and cep + pi/2 (profile kind)
     float cf, sf;           // cos, sin of the polarisation angle
-    float x0, y0, z0, dx, dy, dz, D;   // the grid in float32 (rejection tests)
 };
 
-// Geometry of one replica point given in float32 (xf, yf, zf; rejection) and
-// float64 (X, Y, Z; formed only for points near the shell): false outside the
-// shell; else R (float32), zeta = R - R0 (float64 accuracy) and the angle alpha
-// from the -x axis.
-template <typename XYZ>
-__device__ __forceinline__ bool shell_point(float xf, float yf, float zf, XYZ xyz, const PulseF32& k, float& Rf,
-                                            double& zeta, float& alpha) {
+// Geometry of the replica point X = x0 + i dx + m D, Y = y0 + j dy, Z = z0 + l dz:
+// false outside the shell; else the point (X, Y, Z rounded to float32), R
+// (float32), zeta = R - R0 (double-float, float64-level accuracy) and the angle
+// alpha from the -x axis.  A float32 test rejects points well outside the shell
+// first; for the rest the float32 root of R^2 is refined by one Newton step
+// whose residual R^2 - R_f^2 is formed in double-float.  A point within a
+// relative 1e-6 of the support's edge |zeta| = L/2 (grid points can lie on it
+// exactly, and the closed window then depends on rounding) takes the float64
+// test of the float64 initialiser, so that both storages keep the same points.
+__device__ __forceinline__ bool shell_point(int i, int j, int l, int m, const GridGeom& g, const ShellGeom& sh,
+                                            const PulseF32& k, float3& P, float& Rf, FF& zeta, float& alpha) {
+    const float xf = fmaf((float)i, k.dx.h, k.x0.h) + (float)m * k.D.h;
+    const float yf = fmaf((float)j, k.dy.h, k.y0.h), zf = fmaf((float)l, k.dz.h, k.z0.h);
     const float r2 = xf * xf + yf * yf + zf * zf;
     if (r2 < k.lo2 || r2 > k.hi2) return false;        // well outside the shell (margin 1e-4 in R^2)
-    double X, Y, Z;
-    xyz(X, Y, Z);
-    xf = (float)X; yf = (float)Y; zf = (float)Z;
-    Rf = sqrtf(xf * xf + yf * yf + zf * zf);
+    const FF X = ff_add(ff_add(k.x0, ff_mul_f(k.dx, (float)i)), ff_mul_f(k.D, (float)m));
+    const FF Y = ff_add(k.y0, ff_mul_f(k.dy, (float)j)), Z = ff_add(k.z0, ff_mul_f(k.dz, (float)l));
+    const FF S = ff_add(ff_add(ff_sqr(X), ff_sqr(Y)), ff_sqr(Z));
+    Rf = sqrtf(S.h);
     if (!(Rf > 0.f)) return false;
-    // one Newton step on R^2 = S: R = R_f + (S - R_f^2) / (2 R_f), the residual
-    // exact in float64 (R_f^2 has 48 bits), the correction (~1e-7 R) in float32
-    const double S = fma(X, X, fma(Y, Y, Z * Z));
-    const float corr = (float)(S - (double)Rf * (double)Rf) / (2.f * Rf);
-    zeta = ((double)Rf - k.R0) + (double)corr;
-    if (zeta < -k.halfL || zeta > k.halfL) return false;
-    alpha = atan2f(sqrtf(yf * yf + zf * zf), -xf);
+    const float corr = ff_add(S, ff_neg(two_prod(Rf, Rf))).h / (2.f * Rf);
+    zeta = ff_add(two_sum(Rf, -k.R0.h), two_sum(corr, -k.R0.l));
+    if (fabsf(fabsf(zeta.h) - k.halfL) < 1e-6f * k.halfL) {
+        const double X = (g.x_min + i * g.dx) + m * (g.Nx * g.dx), Y = g.y_min + j * g.dy, Z = g.z_min + l * g.dz;
+        if (!edge_inside(X, Y, Z, sh)) return false;
+    } else if (zeta.h < -k.halfL || zeta.h > k.halfL) {
+        return false;
+    }
+    P = make_float3(X.h, Y.h, Z.h);
+    alpha = atan2f(sqrtf(Y.h * Y.h + Z.h * Z.h), -X.h);
     return true;
 }
 
 // Both carrier amplitudes of one replica point (u1 at phase cep, u2 at
 // cep + pi/2, the latter to be scaled by the ellipticity); false if zero.
-template <typename XYZ>
-__device__ __forceinline__ bool pulse_u_f2(float xf, float yf, float zf, XYZ xyz, const PulseParams& p,
-                                           const PulseF32& k, float& u1, float& u2) {
+__device__ __forceinline__ bool pulse_u_f2(int i, int j, int l, int m, const GridGeom& g, const ShellGeom& sh,
+                                           const PulseParams& p, const PulseF32& k, float3& P, float& u1, float& u2) {
     float Rf, alpha;
-    double zeta;
-    if (!shell_point(xf, yf, zf, xyz, k, Rf, zeta, alpha)) return false;
+    FF zeta;
+    if (!shell_point(i, j, l, m, g, sh, k, P, Rf, zeta, alpha)) return false;
     const float inv_R = 1.f / Rf;
     if (p.kind == 2) {
-        // tabulated profile: the sample index in float64 (a spacing of a few nm
-        // against |zeta| of tens of um), the interpolation weights in float32
+        // tabulated profile: the sample index in double-float (a spacing of a few
+        // nm against |zeta| of tens of um), the interpolation weights in float32
         const float uts = u_ts_flat_f(alpha, k.th, k.eps);
         if (uts == 0.f) return false;
-        const double s = (zeta - k.prof_z0) * k.prof_inv_dz;
-        if (!(s >= 0.0) || s > (double)(p.prof_n - 1)) return false;
-        int ik = (int)s;
-        if (ik > p.prof_n - 2) ik = p.prof_n - 2;
-        const float t = (float)(s - ik);
+        const FF s = ff_mul(ff_add(zeta, ff_neg(k.prof_z0)), k.prof_inv_dz);
+        if (!(s.h >= 0.f) || s.h > (float)(p.prof_n - 1)) return false;
+        int ik = (int)floorf(s.h);
+        float t = (s.h - (float)ik) + s.l;
+        if (t < 0.f) { --ik; t += 1.f; }
+        if (ik < 0) { ik = 0; t = 0.f; }
+        if (ik > p.prof_n - 2) { ik = p.prof_n - 2; t = 1.f; }
         const double2 a0 = p.prof[PSATD_IX(ik, p.prof_n)], a1 = p.prof[PSATD_IX(ik + 1, p.prof_n)];
         const float ar = (float)a0.x + t * (float)(a1.x - a0.x), ai = (float)a0.y + t * (float)(a1.y - a0.y);
         const float A = k.amp * inv_R * uts;
@@ -158,11 +218,12 @@ __device__ __forceinline__ bool pulse_u_f2(float xf, float yf, float zf, XYZ xyz
         u2 = A * (ar * k.cp[1] - ai * k.sp[1]);
         return true;
     }
-    // carrier: the phase k0 zeta + cep reduced to [-pi, pi] in float64
-    const double arg = fma(k.k0, zeta, k.phase);
+    // carrier: the phase k0 zeta + cep reduced to [-pi, pi] in double-float
+    const FF arg = ff_add(ff_mul(k.k0, zeta), k.phase);
+    const FF red = ff_add(arg, ff_neg(ff_mul_f(k.two_pi, rintf(arg.h * k.inv2pi))));
     float sn, cs;
-    sincosf((float)fma(-k.two_pi, rint(arg * k.inv2pi), arg), &sn, &cs);
-    const float zeta_f = (float)zeta;
+    sincosf(red.h + red.l, &sn, &cs);
+    const float zeta_f = zeta.h;
     float A;
     if (p.kind == 0) {
         // flat-top, Eq. 7-8
@@ -222,21 +283,13 @@ __global__ void init_pulse_kernel(void* __restrict__ data, GridGeom g, ShellGeom
             l = (int)(r / g.Ny);
         }
         if constexpr (sizeof(T) == 4) {
-            // float32 coordinates for the rejection test; float64 ones only near the shell
             const float cf = kf.cf, sf = kf.sf;
-            const float xtf = kf.x0 + (float)i * kf.dx, yf = kf.y0 + (float)j * kf.dy, zf = kf.z0 + (float)l * kf.dz;
             float E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
             for (int m = m_lo; m <= m_hi; ++m) {
                 float u1, u2;
-                auto xyz = [&](double& X, double& Y, double& Z) {
-                    X = (g.x_min + i * g.dx) + m * D;
-                    Y = g.y_min + j * g.dy;
-                    Z = g.z_min + l * g.dz;
-                };
-                if (!pulse_u_f2(xtf + (float)m * kf.D, yf, zf, xyz, p, kf, u1, u2)) continue;
-                double X, Y, Z;
-                xyz(X, Y, Z);
-                const float xs = (float)X, ys = (float)Y, zs = (float)Z;
+                float3 P;
+                if (!pulse_u_f2(i, j, l, m, g, sh, p, kf, P, u1, u2)) continue;
+                const float xs = P.x, ys = P.y, zs = P.z;
                 float s0[3], s1[3];
                 if (u1 != 0.f) {
                     pol_vectors_f(xs, ys, zs, 0.f, cf, sf, s0, s1);
@@ -288,17 +341,17 @@ PulseF32 pulse_f32(const PulseParams& p, const ShellGeom& sh, const GridGeom& g)
     k.sps = sin(p.pol_angle);
     k.cf = (float)k.cps;
     k.sf = (float)k.sps;
-    k.x0 = (float)g.x_min; k.y0 = (float)g.y_min; k.z0 = (float)g.z_min;
-    k.dx = (float)g.dx; k.dy = (float)g.dy; k.dz = (float)g.dz;
-    k.D = (float)(g.Nx * g.dx);
-    k.R0 = sh.R0;
-    k.halfL = 0.5 * sh.L;
-    k.k0 = 2.0 * kPi / p.lambda;
-    k.inv2pi = 1.0 / (2.0 * kPi);
-    k.two_pi = 2.0 * kPi;
-    k.phase = p.cep;
-    k.prof_z0 = p.prof_z0;
-    k.prof_inv_dz = p.prof_dz != 0.0 ? 1.0 / p.prof_dz : 0.0;
+    k.x0 = ff_from(g.x_min); k.y0 = ff_from(g.y_min); k.z0 = ff_from(g.z_min);
+    k.dx = ff_from(g.dx); k.dy = ff_from(g.dy); k.dz = ff_from(g.dz);
+    k.D = ff_from(g.Nx * g.dx);
+    k.R0 = ff_from(sh.R0);
+    k.halfL = (float)(0.5 * sh.L);
+    k.k0 = ff_from(2.0 * kPi / p.lambda);
+    k.inv2pi = (float)(1.0 / (2.0 * kPi));
+    k.two_pi = ff_from(2.0 * kPi);
+    k.phase = ff_from(p.cep);
+    k.prof_z0 = ff_from(p.prof_z0);
+    k.prof_inv_dz = ff_from(p.prof_dz != 0.0 ? 1.0 / p.prof_dz : 0.0);
     const float lo = (float)(sh.R0 - 0.5 * sh.L), hi = (float)(sh.R0 + 0.5 * sh.L);
     k.lo2 = lo * lo * 0.9999f;
     k.hi2 = hi * hi * 1.0001f;
