@@ -15,6 +15,7 @@
 // transcendental), and the two carriers of an elliptical pulse (phases cep and
 // cep + pi/2) share one evaluation of the geometry.
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace psatd {
 
@@ -103,49 +104,6 @@ __device__ __forceinline__ float u_ts_flat_f(float a, float th, float eps) {
         return c * c;
     }
     return 0.f;
-}
-
-// Double-float arithmetic: an unevaluated sum h + l of two float32 values
-// (|l| <= ulp(h) / 2), about 48 significant bits from float32 operations only
-// (exact products by fmaf, exact sums by the two-sum of Knuth), so that the
-// float32-storage initialiser needs no float64 arithmetic at all.
-struct FF {
-    float h, l;
-};
-__host__ __device__ __forceinline__ FF ff_from(double v) {
-    FF f;
-    f.h = (float)v;
-    f.l = (float)(v - (double)f.h);
-    return f;
-}
-__device__ __forceinline__ FF two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ FF quick_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ FF two_prod(float a, float b) {
-    const float p = a * b;
-    return {p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    const FF s = two_sum(a.h, b.h);
-    return quick_two_sum(s.h, s.l + (a.l + b.l));
-}
-__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-    const FF p = two_prod(a.h, b.h);
-    return quick_two_sum(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
-}
-__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
-    const FF p = two_prod(a.h, b);
-    return quick_two_sum(p.h, fmaf(a.l, b, p.l));
-}
-__device__ __forceinline__ FF ff_sqr(FF a) {
-    const FF p = two_prod(a.h, a.h);
-    return quick_two_sum(p.h, fmaf(2.f * a.h, a.l, p.l));
 }
 
 // Per-launch constants of the float32-storage evaluation (built on the host).
