@@ -80,8 +80,12 @@ def args_parse():
                     help="append a condensed record of the run to this JSON-lines file "
                          "(default: $PSATD_METRICS_LOG, else none)")
     a = ap.parse_args()
+    a.storage_note = None
     if a.storage == "real" and not real_storage_supported(a.size):
-        a.storage = "complex"          # the real-field kernels cover 256 x 256 x {64, 128, 256}
+        # the real-field kernels cover 256 x 256 x {64, 128, 256}; the line says so
+        a.storage = "complex"
+        a.storage_note = ("real storage requested; the real-field kernels cover 256 x 256 x {64, 128, 256} "
+                          "grids, so this %d^3 run uses complex storage" % a.size)
     return a
 
 
@@ -225,7 +229,8 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(a.size, a.storage),
+        "config": dict(workload_config(a.size, a.storage),
+                       **({"storage_note": a.storage_note} if a.storage_note else {})),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -303,7 +308,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(a.size, a.storage),
+        "config": dict(workload_config(a.size, a.storage),
+                       **({"storage_note": a.storage_note} if a.storage_note else {})),
         "focal_fields_per_s": world * a.steps / (t_max / 1e3),
         "roofline": dict(roof, region="CUDA events around every launch of the same %d jobs, run right after "
                          "the timed region (%.1f ms/job there; the timed region itself runs without per-kernel "
