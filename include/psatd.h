@@ -120,8 +120,9 @@ typedef struct psatd_diag {
  * psatd_sample_focal_plane reads the real field, and psatd_focal_one_shot
  * leaves and samples the half spectrum (k_x >= 0, in the slot order of the
  * real-field plane pass, the x Nyquist modes in a context-owned array; the
- * negative k_x are their conjugates).  Only psatd_diagnostics works through a
- * complex scratch copy, allocated on its first use (48 bytes per cell).
+ * negative k_x are their conjugates); psatd_diagnostics takes the energy from
+ * the real fields and the divergence from the half spectrum of a real copy of
+ * three components (12 bytes per cell, allocated on its first use).
  * Cites: Sec. 2.1 (solver), Sec. 2.3 (periodic layer). */
 psatd_status psatd_init_grid(const psatd_grid* grid, const psatd_mapping* mapping,
                              double dt, int precision, void* cuda_stream, int flags,

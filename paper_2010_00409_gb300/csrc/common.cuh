@@ -306,9 +306,6 @@ cudaError_t launch_plane_rc(float* data, float2* nyq, int ncomp, const GridGeom&
 bool plane_rc_supported(int prec, const GridGeom& g);
 int plane_rc_slot_mode(int p);
 
-// Real <-> complex copies of n values (widen: im = 0; narrow: keep re).
-cudaError_t launch_widen(const float* in, float2* out, size_t n, cudaStream_t s);
-cudaError_t launch_narrow(const float2* in, float* out, size_t n, cudaStream_t s);
 int kspace_tma_box_x(int prec);
 int kspace_tma_box_z(int Nz);
 cudaError_t launch_wait_timeout_selftest(int* err, cudaStream_t s);
@@ -372,6 +369,15 @@ cudaError_t launch_energy(const cplx<T>* data, size_t n_per_comp, double* partia
 template <typename T>
 cudaError_t launch_divergence(const cplx<T>* spec3, const GridGeom& g, const Tables<T>& tb,
                               double* partial, int nblocks, cudaStream_t s, long long* nlaunch);
+// Real float32 storage: the energy from the real fields [6][n], and the
+// divergence maxima of three real components from their half spectrum in slot
+// order (spec [3][Nz][Ny][Nx/2], slot p at wave number slot_k[p]) and x-Nyquist
+// array (nyq [3][Nz][Ny], wave number kx_nyq).
+cudaError_t launch_energy_real(const float* data, size_t n_per_comp, double* partial, int nblocks, cudaStream_t s,
+                               long long* nlaunch);
+cudaError_t launch_divergence_half(const float2* spec, const float2* nyq, const GridGeom& g, const float* slot_k,
+                                   float kx_nyq, const Tables<float>& tb, double* partial, int nblocks,
+                                   cudaStream_t s, long long* nlaunch);
 // Final reduction of `nblocks` rows of `width` doubles: columns [0, nsum) are
 // summed, columns [nsum, width) are max-reduced.  Result in out[width].
 cudaError_t launch_reduce_final(const double* partial, int nblocks, int width, int nsum,

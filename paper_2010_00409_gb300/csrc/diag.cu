@@ -85,6 +85,62 @@ divergence_kernel(const cplx<T>* __restrict__ F, GridGeom g, const T* __restrict
     if (threadIdx.x == 0) { Pt[2 * blockIdx.x] = bd; Pt[2 * blockIdx.x + 1] = bf; }
 }
 
+// Real float32 storage [6][n]: partial[b][0] = sum E^2, partial[b][1] = sum B^2.
+__global__ void __launch_bounds__(kThreads)
+energy_real_kernel(const float* __restrict__ f, size_t n, double* __restrict__ partial) {
+    __shared__ double sh[kThreads / 32];
+    double eE = 0.0, eB = 0.0;
+    const GBuf<const float> F{f, 6LL * (long long)n};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float a = F[i], b = F[n + i], c = F[2 * n + i];
+        eE += (double)fmaf(c, c, fmaf(b, b, a * a));
+        a = F[3 * n + i]; b = F[4 * n + i]; c = F[5 * n + i];
+        eB += (double)fmaf(c, c, fmaf(b, b, a * a));
+    }
+    const double sE = block_sum(eE, sh);
+    const double sB = block_sum(eB, sh);
+    const GBuf<double> Pt{partial, 2LL * gridDim.x};
+    if (threadIdx.x == 0) { Pt[2 * blockIdx.x] = sE; Pt[2 * blockIdx.x + 1] = sB; }
+}
+
+// The spectrum of three real components as the real-field plane kernels leave
+// it: the half spectrum S [3][Nz][Ny][Nx/2] in slot order (slot p has wave
+// number kxs[p]) and the x-Nyquist array Q [3][Nz][Ny] (wave number kx_nyq).
+// The modes with negative k_x mirror the stored ones (F(-k) = conj F(k)), so
+// the maxima over the stored modes are the maxima over the whole spectrum.
+__global__ void __launch_bounds__(kThreads)
+divergence_half_kernel(const float2* __restrict__ S, const float2* __restrict__ Q, GridGeom g,
+                       const float* __restrict__ kxs, float kx_nyq, const float* __restrict__ ky,
+                       const float* __restrict__ kz, double* __restrict__ partial) {
+    __shared__ double sh[kThreads / 32];
+    const int nh = g.Nx / 2, rows = g.Ny * g.Nz;
+    const GBuf<const float2> SF{S, 3LL * rows * nh}, QF{Q, 3LL * rows};
+    float md2 = 0.f, mf2 = 0.f;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int iy = row % g.Ny, iz = row / g.Ny;
+        const float b = ky[PSATD_IX(iy, g.Ny)], c = kz[PSATD_IX(iz, g.Nz)];
+        for (int p = threadIdx.x; p <= nh; p += blockDim.x) {
+            const float a = p < nh ? kxs[PSATD_IX(p, nh)] : kx_nyq;
+            float2 X, Y, Z;
+            if (p < nh) {
+                const size_t i = (size_t)row * nh + p, st = (size_t)rows * nh;
+                X = SF[i]; Y = SF[st + i]; Z = SF[2 * st + i];
+            } else {
+                X = QF[row]; Y = QF[rows + row]; Z = QF[2 * rows + row];
+            }
+            const float k2 = a * a + b * b + c * c;
+            const float dr = a * X.x + b * Y.x + c * Z.x;
+            const float di = a * X.y + b * Y.y + c * Z.y;
+            if (k2 > 0.f) md2 = fmaxf(md2, (dr * dr + di * di) / k2);
+            mf2 = fmaxf(mf2, (float)cell_energy3<float>(X, Y, Z));
+        }
+    }
+    const double bd = block_max(sqrt((double)md2), sh);
+    const double bf = block_max(sqrt((double)mf2), sh);
+    const GBuf<double> Pt{partial, 2LL * gridDim.x};
+    if (threadIdx.x == 0) { Pt[2 * blockIdx.x] = bd; Pt[2 * blockIdx.x + 1] = bf; }
+}
+
 __global__ void reduce_final_kernel(const double* __restrict__ partial, int nblocks, int width, int nsum,
                                     double* __restrict__ out) {
     __shared__ double sh[kThreads / 32];
@@ -115,6 +171,21 @@ template <typename T>
 cudaError_t launch_divergence(const cplx<T>* spec3, const GridGeom& g, const Tables<T>& tb,
                               double* partial, int nblocks, cudaStream_t s, long long* nlaunch) {
     divergence_kernel<T><<<nblocks, kThreads, 0, s>>>(spec3, g, tb.k[0], tb.k[1], tb.k[2], partial);
+    if (nlaunch) ++*nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_real(const float* data, size_t n_per_comp, double* partial, int nblocks, cudaStream_t s,
+                               long long* nlaunch) {
+    energy_real_kernel<<<nblocks, kThreads, 0, s>>>(data, n_per_comp, partial);
+    if (nlaunch) ++*nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divergence_half(const float2* spec, const float2* nyq, const GridGeom& g, const float* slot_k,
+                                   float kx_nyq, const Tables<float>& tb, double* partial, int nblocks,
+                                   cudaStream_t s, long long* nlaunch) {
+    divergence_half_kernel<<<nblocks, kThreads, 0, s>>>(spec, nyq, g, slot_k, kx_nyq, tb.k[1], tb.k[2], partial);
     if (nlaunch) ++*nlaunch;
     return cudaGetLastError();
 }

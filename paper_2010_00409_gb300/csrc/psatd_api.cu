@@ -92,7 +92,6 @@ struct psatd_ctx {
     size_t field_bytes = 0;
     bool own_fields = false;
     bool real_fields = false;           // real float32 storage (PSATD_FLAG_REAL_FIELDS)
-    DevBuf cscratch;                    // real fields: complex copy for init, sampling, diagnostics
     DevBuf slot_k, slot_coef;           // real fields: k_x per slot, coefficient table in slot order
     DevBuf slot_mode;                   // real fields: x mode index per slot (sampling from the half spectrum)
     DevBuf slot_coef_proj;              // real fields: projection table (C = 1/Ntot, S = 0) in slot order
@@ -112,6 +111,7 @@ struct psatd_ctx {
 
     // scratch (device), allocated on first use
     DevBuf diag_spec, diag_partial, diag_out;
+    DevBuf diag_nyq;                    // real fields: the x-Nyquist array of the diagnostics' spectrum
     DevBuf samp_wx, samp_wy, samp_wz, samp_g, samp_h, samp_out;
     int samp_ny = 0, samp_nz = 0;
 
@@ -663,35 +663,6 @@ cudaError_t spectral_pass_real(psatd_ctx* c, const ModeCoef<float>* coef = nullp
     });
 }
 
-// Real fields: operations written for complex storage run on the context's
-// complex scratch copy while a ComplexView is alive.
-struct ComplexView {
-    psatd_ctx* c;
-    void* fields;
-    size_t bytes;
-    explicit ComplexView(psatd_ctx* cc) : c(cc), fields(cc->fields), bytes(cc->field_bytes) {
-        c->fields = c->cscratch.p;
-        c->field_bytes = c->cscratch.bytes;
-        c->real_fields = false;
-    }
-    ~ComplexView() {
-        c->fields = fields;
-        c->field_bytes = bytes;
-        c->real_fields = true;
-    }
-};
-
-// Allocate the complex scratch copy; with widen, fill it from the real fields.
-psatd_status ensure_scratch(psatd_ctx* c, bool widen) {
-    const size_t n = 6 * n_cells(c->grid);
-    CK(c, ensure_buf(c->cscratch, n * sizeof(float2)));
-    if (widen) {
-        CK(c, launch_widen(static_cast<const float*>(c->fields), static_cast<float2*>(c->cscratch.p), n, c->stream));
-        ++c->launches;
-    }
-    return PSATD_OK;
-}
-
 psatd_status upload_slot_tables(psatd_ctx* c) {
     const int nh = c->grid.Nx / 2;
     std::vector<float> k(nh);
@@ -1049,10 +1020,10 @@ void psatd_destroy(psatd_ctx* c) {
     free_buf(c->coef);
     free_buf(c->coef_T);
     free_buf(c->coef_proj);
-    free_buf(c->cscratch); free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
+    free_buf(c->slot_k); free_buf(c->slot_coef); free_buf(c->nyq);
     free_buf(c->slot_mode); free_buf(c->slot_coef_proj);
     for (int a = 0; a < 3; ++a) free_buf(c->tw2[a]);
-    free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out);
+    free_buf(c->diag_spec); free_buf(c->diag_partial); free_buf(c->diag_out); free_buf(c->diag_nyq);
     free_buf(c->lprof);
     free_buf(c->multi);
     free_buf(c->samp_wx); free_buf(c->samp_wy); free_buf(c->samp_wz);
@@ -1386,16 +1357,80 @@ psatd_status psatd_focal_one_shot(psatd_ctx* c, const psatd_pulse* pulse, double
     return PSATD_OK;
 }
 
+namespace {
+
+// Diagnostics of real float32 storage without a complex copy: the energy from
+// the real fields; per field (E, then B) its three components copied to a real
+// scratch, taken to the half spectrum by the real-field plane kernel and the z
+// transform of the slots and of the x-Nyquist array, and the divergence maxima
+// over the stored modes.
+psatd_status diagnostics_real(psatd_ctx* c, double host[6]) {
+    const GridGeom g = geom(c);
+    const Tables<float> tb = tables<float>(c);
+    const size_t n = n_cells(c->grid);
+    const size_t nq = (size_t)3 * c->grid.Nz * c->grid.Ny;
+    CK(c, ensure_buf(c->diag_spec, 3 * n * sizeof(float)));
+    CK(c, ensure_buf(c->diag_nyq, nq * sizeof(float2)));
+    CK(c, ensure_buf(c->diag_partial, (size_t)kDiagBlocks * 2 * sizeof(double)));
+    CK(c, ensure_buf(c->diag_out, 8 * sizeof(double)));
+    double* partial = static_cast<double*>(c->diag_partial.p);
+    double* res = static_cast<double*>(c->diag_out.p);
+    float* spec = static_cast<float*>(c->diag_spec.p);
+    float2* nyq = static_cast<float2*>(c->diag_nyq.p);
+    cudaError_t e = timed(c, PSATD_KERNEL_DIAG, [&] {
+        cudaError_t r = launch_energy_real(static_cast<const float*>(c->fields), n, partial, kDiagBlocks, c->stream,
+                                           &c->launches);
+        if (r != cudaSuccess) return r;
+        return launch_reduce_final(partial, kDiagBlocks, 2, 2, res, c->stream, &c->launches);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy launch");
+    GridGeom gs = g, gq = g;                          // the slots, the x-Nyquist array as complex grids
+    gs.Nx = g.Nx / 2;
+    gq.Nx = g.Ny;
+    gq.Ny = 1;
+    for (int half = 0; half < 2; ++half) {
+        CK(c, cudaMemcpyAsync(spec, static_cast<const float*>(c->fields) + (size_t)3 * half * n, 3 * n * sizeof(float),
+                              cudaMemcpyDeviceToDevice, c->stream));
+        e = timed(c, PSATD_KERNEL_DIAG, [&] {
+            c->launches += 4;
+            cudaError_t r = launch_plane_rc(spec, nyq, 3, g, tb, -1, c->stream);
+            if (r == cudaSuccess)
+                r = launch_fft_axis_fast<float>(reinterpret_cast<cplx<float>*>(spec), 3, gs, tb, 2, -1, c->stream);
+            if (r == cudaSuccess)
+                r = launch_fft_axis_fast<float>(reinterpret_cast<cplx<float>*>(nyq), 3, gq, tb, 2, -1, c->stream);
+            if (r == cudaSuccess)
+                r = launch_divergence_half(reinterpret_cast<const float2*>(spec), nyq, g,
+                                           static_cast<const float*>(c->slot_k.p), (float)(-0.5 * kTwoPi / g.dx), tb,
+                                           partial, kDiagBlocks, c->stream, &c->launches);
+            if (r != cudaSuccess) return r;
+            return launch_reduce_final(partial, kDiagBlocks, 2, 0, res + 2 + 2 * half, c->stream, &c->launches);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "divergence launch");
+    }
+    CK(c, cudaMemcpyAsync(host, res, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PSATD_OK;
+}
+
+}  // namespace
+
 psatd_status psatd_diagnostics(psatd_ctx* c, psatd_diag* out) {
     psatd_status st = check_ctx(c, true, true);
     if (st) return st;
     if (capturing(c)) return fail(c, PSATD_ERR_STATE, "not allowed while a batch is being captured");
     if (!out) return fail(c, PSATD_ERR_ARG, "NULL out");
     if (c->real_fields) {
-        st = ensure_scratch(c, true);
+        double host[6];
+        st = diagnostics_real(c, host);
         if (st) return st;
-        ComplexView v(c);
-        return psatd_diagnostics(c, out);
+        out->energy_E = host[0];
+        out->energy_B = host[1];
+        out->energy = host[0] + host[1];
+        out->max_div_E = host[2];
+        out->max_E_hat = host[3];
+        out->max_div_B = host[4];
+        out->max_B_hat = host[5];
+        return check_device_error(c);
     }
     const size_t n = n_cells(c->grid);
     const size_t es = cplx_size(c->prec);

@@ -90,6 +90,24 @@ def test_real_init_projection_sampling_diagnostics(lib):
     assert rel(s, ref) <= 1e-5
 
 
+def test_real_diagnostics_match_oracle(lib):
+    # a random real field with longitudinal content: energy from the real
+    # storage, divergence maxima from the half spectrum (slots and x-Nyquist array)
+    g = W.GridSpec(256, 256, 64, 0.5, 0.7, 0.3, 0.0, 0.0, 0.0, 1.0)
+    rng = np.random.Generator(np.random.PCG64(17))
+    f = rng.standard_normal((6, 64, 256, 256)).astype(np.float32)
+    f[1] *= 0.5                                      # uneven components
+    with lib.Context(g, None, 0.2, 32, real=True) as ctx:
+        ctx.set_fields(f)
+        d = ctx.diagnostics()
+        assert np.array_equal(ctx.get_field(-1), f)     # the diagnostics leave the storage unchanged
+    od = O.diagnostics(f.astype(np.complex128), ogrid(g))
+    for k in ("energy", "energy_E", "energy_B"):
+        assert abs(d[k] / od[k] - 1) <= 1e-6, k
+    for k in ("max_div_E", "max_E_hat", "max_div_B", "max_B_hat"):
+        assert abs(d[k] / od[k] - 1) <= 1e-5, (k, d[k], od[k])
+
+
 def test_real_fields_argument_and_state_errors(lib):
     g = W.GridSpec(256, 256, 64, 0.5, 0.5, 0.5, 0.0, 0.0, 0.0, 1.0)
     with pytest.raises(lib.PsatdError):
