@@ -28,18 +28,27 @@ template <typename T, int N1, int N2> struct RowsCfg {
 };
 
 // columns per block for the strided kernel: 128 contiguous bytes per row of the
-// tile, halved until the exchange buffer fits the shared-memory budget: 48 KB
-// along y (rows one plane row apart), 128 KB along z, whose rows lie a whole
-// plane apart (at 1024^2 planes, 32-byte runs 8 MB apart used the DRAM bursts
-// poorly: the z transforms took 2.3 times as long as with 128-byte runs)
+// tile, halved until the exchange buffer fits the shared-memory budget.  Along
+// z, whose rows lie a whole plane apart, 128 KB (at 1024^2 planes, 32-byte runs
+// 8 MB apart used the DRAM bursts poorly: the z transforms took 2.3 times as
+// long as with 128-byte runs, and 64-byte runs at two blocks per SM 1.16
+// times).  Along y (rows one plane row apart) 48 KB, or 64 KB for 1024-point
+// columns: eight columns, 256 threads held to 128 registers so that two blocks
+// share an SM (at 1024^3, 47.1 against 51.4 ms per step in one process for four
+// columns at 166 registers, three blocks per SM).
 #ifndef PSATD_COLS_Y_BUDGET
 #define PSATD_COLS_Y_BUDGET (48 * 1024)
 #endif
 template <typename T, int N, bool ZAXIS> constexpr int cols_width() {
-    const int budget = ZAXIS ? 128 * 1024 : PSATD_COLS_Y_BUDGET;
+    const int budget = ZAXIS ? 128 * 1024 : (N >= 1024 ? 64 * 1024 : PSATD_COLS_Y_BUDGET);
     int w = 128 / (int)sizeof(cplx<T>);
     while (w > 1 && N * w * (int)sizeof(cplx<T>) > budget) w /= 2;
     return w;
+}
+// 1024-point columns: blocks per SM for the launch bounds, so that 512 threads
+// share the register file (at most 128 registers a thread)
+template <int N, int THREADS> constexpr int cols_min_blocks() {
+    return (N >= 1024 && THREADS < 512) ? 512 / THREADS : 1;
 }
 
 template <typename T, int N1, int N2, int S>
@@ -91,7 +100,7 @@ fft_rows_kernel(cplx<T>* __restrict__ data, long long rows, const cplx<T>* __res
 // Block = W columns x N2 threads (c fastest).  Tile g -> (comp, o, x-tile);
 // element n of column c at base + n*stride + c.
 template <typename T, int N1, int N2, int W, int S>
-__global__ void __launch_bounds__(W * N2)
+__global__ void __launch_bounds__(W * N2, cols_min_blocks<N1 * N2, W * N2>())
 fft_cols_kernel(cplx<T>* __restrict__ data, int Nx, int Ny, int Nz, int axis, const cplx<T>* __restrict__ tw) {
     constexpr int RS = N2 * W, ES = W;
     extern __shared__ __align__(16) unsigned char cols_smem[];
