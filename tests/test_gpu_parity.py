@@ -299,7 +299,7 @@ def test_tight_focus_256_full_size_real_fields(lib, focus_reference):
 # and against the generic shared-memory kernels on the same inputs.
 # ---------------------------------------------------------------------------
 FAST_SHAPES = [(64, 64, 64), (256, 64, 128), (128, 256, 64), (64, 128, 256), (512, 16, 64), (48, 64, 128),
-               (1024, 4, 8), (8, 1024, 4), (8, 4, 1024), (4, 8, 512)]
+               (1024, 4, 8), (8, 1024, 4), (8, 4, 1024), (4, 8, 512), (16, 512, 4), (32, 1024, 2)]
 
 
 @pytest.mark.parametrize("prec", [64, 32])
